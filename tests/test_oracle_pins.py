@@ -1,0 +1,489 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own arithmetic: closed forms
+(Fourier symbol of the linear scheme, exact Riemann solution, constant-density
+maximum-entropy solution), invariants (constant states, conservation,
+transposition, partition independence, exact shift) and library routines
+(numpy Gauss-Legendre, scipy adaptive quadrature).  They are chosen so that a
+dropped term, a wrong sign or index or a transposed operand in the oracle
+fails at least one of them.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from oracle import riemann
+from tests.helpers import oracle_problem, rel_l1, rel_linf, transpose_state
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _state(d, prim):
+    P = oracle_problem(d)
+    return P, oracle.prim_to_cons(P, prim)
+
+
+# --------------------------------------------------------------- quadrature
+@pytest.mark.parametrize("Q", [1, 2, 5, 16, 32, 48])
+def test_gauss_legendre_matches_numpy(oracle_mod, Q):
+    x, w = oracle.gauss_legendre(Q)
+    t, wt = np.polynomial.legendre.leggauss(Q)
+    np.testing.assert_allclose(x, 0.5 * (t + 1.0), rtol=0, atol=2e-15)
+    np.testing.assert_allclose(w, 0.5 * wt, rtol=0, atol=2e-15)
+
+
+# --------------------------------------------------------------- constant states
+@pytest.mark.parametrize("mode", ["plain", "literal"])
+@pytest.mark.parametrize("bc", ["periodic", "transmissive", "dirichlet"])
+@pytest.mark.parametrize("system", ["advection", "euler", "spray"])
+def test_constant_state_preserved_bitwise(oracle_mod, system, bc, mode):
+    """F~(W, W, n) = F(W).n, so every face difference vanishes exactly."""
+    nx, ny = 13, 9
+    if system == "advection":
+        const = [1.37]
+        params = (0.8, -0.35)
+    elif system == "euler":
+        const = [1.3, 0.4 * 1.3, -0.25 * 1.3, 2.5]
+        params = (1.4,)
+    else:
+        const = [1.0, 0.55, 0.4, 0.31, 0.4 * 0.3, 0.4 * -0.2]
+        params = (0.0, 0.0, 0.0, 32.0, 1e-13)  # transport only
+    W0 = np.empty((len(const), ny, nx))
+    for v, c in enumerate(const):
+        W0[v] = c
+    d = wl.problem(system, nx, ny, bc=(bc,) * 4, params=params, npart_x=3, npart_y=2,
+                   bc_state=(tuple(const),) * 4)
+    P = oracle_problem(d)
+    r = oracle.run(P, W0, 7, mode=mode)
+    assert r.status == oracle.OK and r.steps == 7
+    assert np.array_equal(r.W, W0)
+
+
+# --------------------------------------------------------------- conservation
+@pytest.mark.parametrize("system", ["euler", "spray_transport"])
+def test_periodic_conservation(oracle_mod, system):
+    """Fluxes telescope on a periodic grid: every variable's total is
+    conserved to 1e-13 relative to its L1 mass."""
+    if system == "euler":
+        prim, d = wl.random_smooth_euler(48, seed=3, ny=40)
+    else:
+        prim, d = wl.spray_field(40)
+        d = dict(d, params=(0.0, 0.0, 0.0, 32.0, 1e-13))
+    P, W0 = _state(d, prim)
+    t0 = oracle.totals(P, W0)
+    r = oracle.run(P, W0, 60)
+    assert r.status == oracle.OK
+    t1 = oracle.totals(P, r.W)
+    mass = np.array([np.abs(W0[v]).sum() * P.dx * P.dy for v in range(P.nvar)])
+    assert np.all(np.abs(t1 - t0) / mass <= 1e-13), np.abs(t1 - t0) / mass
+
+
+def test_transmissive_budget_identity(oracle_mod):
+    """On transmissive sides the ghost equals the border cell, so the boundary
+    face flux is F(W_border).n and the total changes by -dt times the net
+    outflow through the four sides."""
+    prim, d = wl.random_smooth_euler(24, seed=5, ny=20)
+    d = dict(d, bc=("transmissive",) * 4)
+    P, W0 = _state(d, prim)
+    r = oracle.run(P, W0, 1)
+    dt = r.dts[0]
+    nvar, ny, nx = W0.shape
+    out = np.zeros(nvar)
+    for j in range(ny):
+        fe, _ = oracle.phys_flux(P, W0[:, j, nx - 1], (1.0, 0.0))
+        fw, _ = oracle.phys_flux(P, W0[:, j, 0], (1.0, 0.0))
+        out += (fe - fw) * P.dy
+    for i in range(nx):
+        fn, _ = oracle.phys_flux(P, W0[:, ny - 1, i], (0.0, 1.0))
+        fs, _ = oracle.phys_flux(P, W0[:, 0, i], (0.0, 1.0))
+        out += (fn - fs) * P.dx
+    dtot = oracle.totals(P, r.W) - oracle.totals(P, W0)
+    scale = np.array([np.abs(W0[v]).sum() * P.dx * P.dy for v in range(nvar)])
+    np.testing.assert_array_less(np.abs(dtot + dt * out) / scale, 1e-13)
+
+
+# --------------------------------------------------------------- advection closed form
+def _advection_symbol(nx, ny, nu_x, nu_y, ax, ay):
+    """Amplification factor of the first-order upwind scheme (the LF flux
+    with sigma = |a.n| is upwind): u_i - |nu| (u_i - u_{i-s})."""
+    kx = np.fft.fftfreq(nx) * 2.0 * math.pi
+    ky = np.fft.fftfreq(ny) * 2.0 * math.pi
+    sx = np.exp(-1j * np.sign(ax) * kx)[None, :]
+    sy = np.exp(-1j * np.sign(ay) * ky)[:, None]
+    return 1.0 - abs(nu_x) * (1.0 - sx) - abs(nu_y) * (1.0 - sy)
+
+
+@pytest.mark.parametrize("case", ["c1", "rect_neg"])
+def test_advection_fourier_closed_form(oracle_mod, case):
+    """The scheme is linear with constant coefficients: W^N = IFFT(G^N FFT(W^0)),
+    G = 1 - nu_x (1 - e^{-i kx}) - nu_y (1 - e^{-i ky})."""
+    if case == "c1":
+        prim, d = wl.advection_bump(128)
+        nsteps = 100
+    else:
+        x = wl.centres(96)
+        y = wl.centres(64)
+        prim = (1.0 + np.sin(2 * np.pi * x)[None, :] * np.cos(4 * np.pi * y)[:, None] ** 3)[None]
+        d = wl.problem("advection", 96, 64, cfl=0.45, params=(-0.7, 0.3))
+        nsteps = 80
+    P, W0 = _state(d, prim)
+    r = oracle.run(P, W0, nsteps)
+    assert r.status == oracle.OK
+    ax, ay = d["params"]
+    lmax = max(abs(ax), abs(ay))
+    dt = d["cfl"] * min(P.dx, P.dy) / lmax
+    np.testing.assert_allclose(r.dts, dt, rtol=1e-15)
+    G = _advection_symbol(P.nx, P.ny, ax * dt / P.dx, ay * dt / P.dy, ax, ay)
+    exact = np.real(np.fft.ifft2(np.fft.fft2(W0[0]) * G ** nsteps))
+    assert np.max(np.abs(r.W[0] - exact)) / np.max(np.abs(exact)) < 1e-13
+    if case == "c1":
+        # dyadic steps: dt = 0.5/128 exactly, nu_x = 1/2, nu_y = 1/4
+        assert r.dts[0] == 0.5 / 128
+        # discrete maximum principle
+        assert r.W.min() >= W0.min() - 1e-15 and r.W.max() <= W0.max() + 1e-15
+
+
+# --------------------------------------------------------------- exact shift
+def _quantised_bump(n):
+    x = wl.centres(n)
+    y = wl.centres(n)
+    u = 1.0 + 0.9 * np.exp(-((x[None, :] - 0.4) ** 2 + (y[:, None] - 0.55) ** 2) / 0.02)
+    return (np.round(u * 2.0 ** 40) / 2.0 ** 40)[None]
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+@pytest.mark.parametrize("mode", ["plain", "literal"])
+def test_exact_shift_cfl1(oracle_mod, axis, mode):
+    """CFL = 1 along one axis is an exact one-cell shift (every intermediate
+    is exact for data on a 2^-40 grid in [1, 2))."""
+    n = 40
+    W0 = _quantised_bump(n)
+    a = (1.0, 0.0) if axis == "x" else (0.0, 1.0)
+    d = wl.problem("advection", n, n, cfl=1.0, params=a, npart_x=3, npart_y=2)
+    P = oracle_problem(d)
+    r = oracle.run(P, W0, 17, mode=mode)
+    assert r.status == oracle.OK
+    expect = np.roll(W0, 17, axis=2 if axis == "x" else 1)
+    assert np.array_equal(r.W, expect)
+
+
+def test_exact_shift_generic_data_ulps(oracle_mod):
+    """Generic FP64 data: the shift holds to rounding (a few ulp per step)."""
+    n = 32
+    rng = np.random.default_rng(11)
+    W0 = rng.uniform(0.5, 3.0, size=(1, n, n))
+    P = oracle_problem(wl.problem("advection", n, n, cfl=1.0, params=(1.0, 0.0)))
+    r = oracle.run(P, W0, 50)
+    expect = np.roll(W0, 50, axis=2)
+    assert np.max(np.abs(r.W - expect) / np.abs(expect)) < 50 * 4 * 2.0 ** -52
+
+
+def test_dirichlet_inflow_shift(oracle_mod):
+    """With a Dirichlet west state and CFL = 1 along +x, the prescribed state
+    enters one cell per step."""
+    n = 24
+    W0 = _quantised_bump(n)
+    d = wl.problem("advection", n, n, cfl=1.0, params=(1.0, 0.0),
+                   bc=("transmissive", "periodic", "dirichlet", "periodic"),
+                   bc_state=((0.0,), (0.0,), (1.25,), (0.0,)), npart_x=2, npart_y=3)
+    P = oracle_problem(d)
+    for mode in ("plain", "literal"):
+        r = oracle.run(P, W0, 5, mode=mode)
+        assert np.all(r.W[0, :, :5] == 1.25)
+        assert np.array_equal(r.W[0, :, 5:], W0[0, :, :-5])
+
+
+# --------------------------------------------------------------- symmetry
+@pytest.mark.parametrize("mode", ["plain", "literal"])
+def test_transposition_bitwise(oracle_mod, mode):
+    """Swapping x and y (and the momentum components) commutes with the step."""
+    prim, d = wl.random_smooth_euler(30, seed=7, ny=22)
+    d = dict(d, bc=("transmissive", "periodic", "transmissive", "periodic"), npart_x=3, npart_y=2)
+    P, W0 = _state(d, prim)
+    r = oracle.run(P, W0, 25, mode=mode)
+    dt_ = dict(d, nx=d["ny"], ny=d["nx"], bc=("periodic", "transmissive", "periodic", "transmissive"),
+               npart_x=2, npart_y=3)
+    Pt = oracle_problem(dt_)
+    rt = oracle.run(Pt, transpose_state(W0, "euler"), 25, mode=mode)
+    assert np.array_equal(transpose_state(rt.W, "euler"), r.W)
+
+
+def test_four_quadrant_is_transpose_symmetric(oracle_mod):
+    """The four-quadrant data maps onto itself under x <-> y, u <-> v, so the
+    solution must equal its own transpose bit for bit."""
+    prim, d = wl.four_quadrant(64, npart=4)
+    P, W0 = _state(d, prim)
+    assert np.array_equal(transpose_state(W0, "euler"), W0)
+    r = oracle.run(P, W0, 40)
+    assert r.status == oracle.OK
+    assert np.array_equal(transpose_state(r.W, "euler"), r.W)
+
+
+# --------------------------------------------------------------- partition
+@pytest.mark.parametrize("parts", [(1, 1), (2, 3), (5, 4), (7, 1), (37, 29)])
+@pytest.mark.parametrize("bc", ["periodic", "transmissive", "dirichlet"])
+def test_partition_literal_equals_plain(oracle_mod, parts, bc):
+    """The overlap copies make the result independent of NPartX x NPartY,
+    including unbalanced splits; literal tasks agree with the plain loop."""
+    prim, d = wl.random_smooth_euler(37, seed=13, ny=29)
+    state = (1.1, 0.2, -0.1, 2.4)
+    d = dict(d, bc=(bc,) * 4, bc_state=(state,) * 4, npart_x=parts[0], npart_y=parts[1])
+    P, W0 = _state(d, prim)
+    a = oracle.run(P, W0, 12, mode="plain")
+    b = oracle.run(P, W0, 12, mode="literal")
+    assert a.status == b.status == oracle.OK
+    assert np.array_equal(a.W, b.W)
+    assert np.array_equal(a.dts, b.dts)
+
+
+def test_partition_literal_spray(oracle_mod):
+    prim, d = wl.spray_field(24)
+    d = dict(d, npart_x=3, npart_y=5)
+    P, W0 = _state(d, prim)
+    a = oracle.run(P, W0, 4, mode="plain")
+    b = oracle.run(P, W0, 4, mode="literal")
+    assert a.status == b.status == oracle.OK
+    assert np.array_equal(a.W, b.W)
+
+
+# --------------------------------------------------------------- Sod / 1D reduction
+def test_exact_riemann_solver_golden(oracle_mod):
+    vals = {}
+    with open(os.path.join(GOLDEN, "sod_star_state.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    ps, us = riemann.star_state(wl.SOD_LEFT, wl.SOD_RIGHT)
+    assert abs(ps - vals["p_star"]) < 6e-6
+    assert abs(us - vals["u_star"]) < 6e-6
+    rho, _, _ = riemann.sample(wl.SOD_LEFT, wl.SOD_RIGHT, np.array([us - 1e-9, us + 1e-9]))
+    assert abs(rho[0] - vals["rho_star_left"]) < 6e-6
+    assert abs(rho[1] - vals["rho_star_right"]) < 6e-6
+
+
+def test_exact_riemann_rankine_hugoniot(oracle_mod):
+    """The sampled exact solution satisfies the jump conditions across the
+    right-moving shock of the Sod problem."""
+    g = 1.4
+    ps, us = riemann.star_state(wl.SOD_LEFT, wl.SOD_RIGHT)
+    rr, ur, pr = wl.SOD_RIGHT
+    xi = np.linspace(0.0, 3.0, 30001)
+    rho, u, p = riemann.sample(wl.SOD_LEFT, wl.SOD_RIGHT, xi)
+    k = np.argmax(rho < rr * 1.0001)  # first point ahead of the shock
+    s = 0.5 * (xi[k - 1] + xi[k])
+    rl, ul, pl = rho[k - 1], u[k - 1], p[k - 1]
+    El = pl / (g - 1) + 0.5 * rl * ul * ul
+    Er = pr / (g - 1) + 0.5 * rr * ur * ur
+    flux = lambda r_, u_, p_, E_: np.array([r_ * u_, r_ * u_ * u_ + p_, u_ * (E_ + p_)])
+    jump = flux(rl, ul, pl, El) - flux(rr, ur, pr, Er) - s * np.array([rl - rr, rl * ul - rr * ur, El - Er])
+    assert np.max(np.abs(jump)) < 2e-4
+
+
+def test_sod_first_order_convergence(oracle_mod):
+    """y-constant Sod data: every row evolves identically (y-fluxes cancel
+    exactly) and the L1 error to the exact solution at t = 0.2 falls with an
+    observed order >= 0.5 (a contact discontinuity limits first-order
+    schemes to between h^(1/2) and h)."""
+    errs = []
+    ns = [100, 200, 400, 800]
+    for n in ns:
+        prim, d = wl.sod_x(n, ny=3)
+        P, W0 = _state(d, prim)
+        r = oracle.run(P, W0, 100000, t_end=0.2)
+        assert r.status == oracle.OK and abs(r.t - 0.2) < 1e-14
+        for j in range(1, 3):
+            assert np.array_equal(r.W[:, j], r.W[:, 0])
+        assert np.all(r.W[2, 0] == 0.0)
+        edges = np.linspace(0.0, 1.0, n + 1)
+        rho, m, E = riemann.cell_average(wl.SOD_LEFT, wl.SOD_RIGHT, edges, 0.5, 0.2)
+        err = (np.abs(r.W[0, 0] - rho).sum() + np.abs(r.W[1, 0] - m).sum() +
+               np.abs(r.W[3, 0] - E).sum()) / n
+        errs.append(err)
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(len(errs) - 1)]
+    assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:]))
+    assert min(orders) >= 0.5, orders
+    assert errs[-1] < 0.05, errs
+
+
+# --------------------------------------------------------------- Euler convergence (Fig. Convergence)
+@pytest.mark.parametrize("case", ["vortex", "cosine"])
+def test_euler_mesh_convergence_order(oracle_mod, case):
+    """Sec. 5.1.3: on the paper's smooth cases the scheme converges at first
+    order (slopes near 0.95 in L1 on the finest grids)."""
+    T = 0.1
+    errs = []
+    ns = [64, 128, 256]
+    for n in ns:
+        if case == "vortex":
+            prim, d = wl.isentropic_vortex(n)
+            ex, _ = wl.isentropic_vortex(n, t=T)
+            exact_rho = ex[0]
+        else:
+            prim, d = wl.localized_cosine(n, repaired=True)
+            exact_rho = wl.localized_cosine_exact(n, T, repaired=True)
+        P, W0 = _state(d, prim)
+        r = oracle.run(P, W0, 100000, t_end=T)
+        assert r.status == oracle.OK
+        errs.append(np.abs(r.W[0] - exact_rho).mean())
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(len(errs) - 1)]
+    assert 0.8 <= orders[-1] <= 1.1, orders
+
+
+# --------------------------------------------------------------- maximum entropy
+@pytest.mark.parametrize("C", [0.3, 1.0, 2.7])
+def test_maxent_constant_density(oracle_mod, C):
+    """n(S) = C has m_{k/2} = C / (1 + k/2): lam = (-ln C, 0, 0, 0),
+    n(0) = C and m_{-1/2} = 2 C."""
+    m = np.array([C / (1 + k / 2) for k in range(4)])
+    st, lam, n0, mmh, it = oracle.maxent(m)
+    assert st == oracle.OK
+    np.testing.assert_allclose(lam, [-math.log(C), 0, 0, 0], atol=1e-12)
+    assert abs(n0 - C) < 1e-12 * C
+    assert abs(mmh - 2 * C) < 1e-12 * C
+
+
+@pytest.mark.parametrize("lam_true", [(0.2, -1.0, 2.0, -0.5), (1.5, 3.0, -6.0, 4.0),
+                                      (-0.7, 0.5, 1.0, 1.5)])
+def test_maxent_recovers_known_density(oracle_mod, lam_true):
+    """Moments of a known exponential density computed by scipy's adaptive
+    quadrature in S are reconstructed to the same multipliers; n(0) and
+    m_{-1/2} match scipy's values."""
+    from scipy.integrate import quad
+    lt = np.array(lam_true)
+    n = lambda S: math.exp(-(lt[0] + lt[1] * S ** 0.5 + lt[2] * S + lt[3] * S ** 1.5))
+    m = np.array([quad(lambda S: S ** (k / 2) * n(S), 0, 1, epsabs=0, epsrel=2e-14, limit=200)[0]
+                  for k in range(4)])
+    assert oracle.realizable(m)
+    st, lam, n0, mmh, it = oracle.maxent(m, Q=48)
+    assert st == oracle.OK
+    np.testing.assert_allclose(lam, lt, atol=1e-8)
+    assert abs(n0 - n(0.0)) < 1e-9 * n(0.0)
+    ref = quad(lambda S: n(S), 0, 1, weight="alg", wvar=(-0.5, 0.0), epsabs=0, epsrel=2e-14)[0]
+    assert abs(mmh - ref) < 1e-9 * ref
+
+
+def test_maxent_round_trip_from_canonical_moments(oracle_mod):
+    """Moments drawn through canonical moments are realizable; the
+    reconstructed density reproduces them (independent quadrature)."""
+    from scipy.integrate import quad
+    rng = np.random.default_rng(21)
+    for _ in range(6):
+        p = rng.uniform(0.2, 0.8, size=3)
+        m = np.array(wl.canonical_to_moments(rng.uniform(0.5, 1.5), *p))
+        assert oracle.realizable(m)
+        st, lam, n0, mmh, it = oracle.maxent(m, Q=48)
+        assert st == oracle.OK and it < 60
+        n = lambda S: math.exp(-(lam[0] + lam[1] * S ** 0.5 + lam[2] * S + lam[3] * S ** 1.5))
+        back = np.array([quad(lambda S: S ** (k / 2) * n(S), 0, 1, epsabs=0, epsrel=1e-13,
+                              limit=200)[0] for k in range(4)])
+        np.testing.assert_allclose(back, m, rtol=1e-9)
+
+
+def test_realizability_rejects_outside_points(oracle_mod):
+    assert oracle.realizable([1.0, 0.5, 1 / 3, 0.25])
+    assert not oracle.realizable([1.0, 0.5, 0.25, 0.125])      # Dirac at 1/2: boundary
+    assert not oracle.realizable([1.0, 0.5, 0.2, 0.1])         # variance < 0
+    assert not oracle.realizable([1.0, 1.2, 1.3, 1.4])
+
+
+def test_spray_evaporation_constant_density(oracle_mod):
+    """For n(S) = C, every moment loses K C per unit time at first
+    (d/dt int_0^{1-Kt} S^{k/2} C dS = -K C at t = 0), so one forward-Euler
+    source step lowers each of m0..m3/2 by K C dt; with u = 0 and u_g = 0 the
+    momenta stay zero."""
+    C, K, dt = 0.8, 0.3, 0.01
+    m = [C / (1 + k / 2) for k in range(4)]
+    P = oracle_problem(wl.problem("spray", 4, 4, params=(K, 0.0, 0.0, 32.0, 1e-13)))
+    st, w = oracle.spray_source_cell(P, dt, 0.3, 0.6, m + [0.0, 0.0])
+    assert st == oracle.OK
+    np.testing.assert_allclose(w[:4], np.array(m) - K * C * dt, rtol=0, atol=1e-14)
+    assert w[4] == 0.0 and w[5] == 0.0
+
+
+def test_spray_drag_geometric_decay(oracle_mod):
+    """Uniform field, no evaporation, gas at rest: u relaxes geometrically,
+    u_N = u_0 (1 - dt m0 / (m1 theta))^N, with no spurious transport."""
+    n = 8
+    m = wl.canonical_to_moments(1.2, 0.5, 0.4, 0.6)
+    prim = np.empty((6, n, n))
+    for k in range(4):
+        prim[k] = m[k]
+    prim[4] = 0.3
+    prim[5] = -0.2
+    theta = 0.5
+    d = wl.problem("spray", n, n, fixed_dt=0.002, params=(0.0, theta, 0.0, 32.0, 1e-13))
+    P, W0 = _state(d, prim)
+    r = oracle.run(P, W0, 30)
+    assert r.status == oracle.OK
+    fac = (1.0 - 0.002 * m[0] / (m[2] * theta)) ** 30
+    np.testing.assert_allclose(r.W[4] / r.W[2], 0.3 * fac, rtol=1e-12)
+    np.testing.assert_allclose(r.W[5] / r.W[2], -0.2 * fac, rtol=1e-12)
+    for k in range(4):
+        assert np.all(r.W[k] == m[k])
+
+
+def test_spray_transport_reduces_to_advection(oracle_mod):
+    """K = 0, no drag and a uniform velocity: each moment is advected like the
+    scalar scheme, so the Fourier closed form applies to every variable."""
+    n = 48
+    prim, _ = wl.spray_field(n)
+    prim[4] = 0.6
+    prim[5] = -0.3
+    d = wl.problem("spray", n, n, cfl=0.4, params=(0.0, 0.0, 0.0, 32.0, 1e-13))
+    P, W0 = _state(d, prim)
+    r = oracle.run(P, W0, 40)
+    assert r.status == oracle.OK
+    dt = 0.4 * P.dx / 0.6
+    np.testing.assert_allclose(r.dts, dt, rtol=1e-14)
+    G = _advection_symbol(n, n, 0.6 * dt / P.dx, -0.3 * dt / P.dy, 0.6, -0.3)
+    for v in range(6):
+        exact = np.real(np.fft.ifft2(np.fft.fft2(W0[v]) * G ** 40))
+        assert np.max(np.abs(r.W[v] - exact)) / np.max(np.abs(exact)) < 1e-12
+
+
+# --------------------------------------------------------------- time step policy
+def test_fixed_dt_cfl_violation(oracle_mod):
+    """Paper mode: a fixed dt is checked against Eq. (CFL_cond) before every
+    step; a violation stops with the state untouched."""
+    prim, d = wl.random_smooth_euler(16, seed=2)
+    P, W0 = _state(d, prim)
+    lmax = oracle.lambda_max(P, W0)
+    ok = oracle.run(oracle_problem(d, fixed_dt=0.99 * P.dx / lmax), W0, 1)
+    assert ok.status == oracle.OK and ok.steps == 1
+    bad = oracle.run(oracle_problem(d, fixed_dt=1.01 * P.dx / lmax), W0, 3)
+    assert bad.status == oracle.ERR_CFL and bad.steps == 0
+    assert np.array_equal(bad.W, W0)
+
+
+def test_adaptive_dt_uses_axis_wave_speeds(oracle_mod):
+    """lmax = max over cells of max(|u| + c, |v| + c) (axis normals)."""
+    prim, d = wl.random_smooth_euler(20, seed=9)
+    P, W0 = _state(d, prim)
+    rho, u, v, p = prim
+    c = np.sqrt(1.4 * p / rho)
+    lm = np.max(np.maximum(np.abs(u), np.abs(v)) + c)
+    assert abs(oracle.lambda_max(P, W0) - lm) < 1e-14 * lm
+    r = oracle.run(P, W0, 1)
+    assert abs(r.dts[0] - 0.4 * P.dx / lm) < 1e-15 * r.dts[0] * 10
+
+
+def test_zero_wave_speed_is_an_error(oracle_mod):
+    W0 = np.ones((1, 8, 8))
+    P = oracle_problem(wl.problem("advection", 8, 8, params=(0.0, 0.0)))
+    r = oracle.run(P, W0, 1)
+    assert r.status == oracle.ERR_ARG and r.steps == 0
+
+
+def test_nonphysical_state_detected(oracle_mod):
+    prim, d = wl.random_smooth_euler(12, seed=4)
+    P, W0 = _state(d, prim)
+    W0[3, 5, 5] = -1.0  # negative energy -> p < 0 -> NaN sound speed
+    r = oracle.run(P, W0, 2)
+    assert r.status == oracle.ERR_NONPHYSICAL and r.steps == 0
