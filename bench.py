@@ -1,0 +1,346 @@
+"""Benchmark of the fused finite-volume step on one GB300 (or N replicas).
+
+Workload (default): 2D Euler, gamma = 1.4, 8192 x 8192 cells, periodic,
+seeded smooth sinusoidal data, CFL 0.4; one bench step = one job of 100
+time steps advanced by fv_run from a state resident in HBM.  The headline
+`value` is FP32-bulk cell-updates/s; the FP64-plain figure of the same job is
+reported beside it under "fp64".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c3|c2|c1|c4|c5] [--no-cpu-baseline] [--no-e2e]
+
+Under torchrun (N > 1) every rank runs an independent replica (the grid is
+not sharded across GPUs): value = all ranks' cell-updates / max rank time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the oracle is the only reference there is).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+WORKLOADS = {
+    # name: (builder, steps per job, description)
+    "c3": (lambda: wl.smooth_periodic(8192), 100,
+           "euler 8192x8192 periodic smooth sinusoids, CFL 0.4, 100 steps"),
+    "c2": (lambda: wl.four_quadrant(2048, npart=8), 500,
+           "euler 2048x2048 four-quadrant Riemann, 8x8 subdomains, transmissive, CFL 0.4, 500 steps"),
+    "c1": (lambda: wl.advection_bump(128), 100,
+           "advection 128x128 a=(1,0.5) periodic, CFL 0.5, 100 steps"),
+}
+
+BYTES_PER_CELL = {"advection": 1, "euler": 4, "spray": 6}  # nvar
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_run(name, d, prim, sample_steps=None, seconds_target=15.0):
+    """Time the FP64 oracle, as it stands, on the host cores on a bounded
+    sample of the workload (a few steps on the full grid)."""
+    import oracle
+    from tests.helpers import oracle_problem
+    oracle.build()
+    P = oracle_problem(d)
+    W0 = oracle.prim_to_cons(P, prim)
+    threads = oracle.max_threads()
+    ncell = d["nx"] * d["ny"]
+    # one probe step to size the sample
+    t = time.perf_counter()
+    r = oracle.run(P, W0, 1)
+    one = time.perf_counter() - t
+    steps = sample_steps or max(1, min(50, int(seconds_target / max(one, 1e-6))))
+    t = time.perf_counter()
+    r = oracle.run(P, r.W, steps)
+    el = time.perf_counter() - t
+    return {"value": ncell * steps / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"{name}: full {d['nx']}x{d['ny']} grid, {steps} FP64 steps (plain mode) after one "
+                      f"warm-up step, {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    build, nsteps_job, desc = WORKLOADS[args.workload]
+    prim, d = build()
+    import oracle
+    from tests.helpers import oracle_problem
+    oracle.build()
+    P = oracle_problem(d)
+    W = oracle.prim_to_cons(P, prim)
+    ncell = d["nx"] * d["ny"]
+    # each step: a bounded sample of the job (a few FV steps of the full grid)
+    t = time.perf_counter()
+    oracle.run(P, W, 1)
+    one = time.perf_counter() - t
+    per = max(1, int(8.0 / max(one, 1e-6)))
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.run(P, W, 1)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = oracle.run(P, W, per)
+        times.append(time.perf_counter() - t)
+        W = r.W
+    el = sum(times)
+    value = ncell * per * args.steps / el
+    line = {"impl": "reference", "metric": "cell-updates/s (FP64 CPU oracle)", "value": value,
+            "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample_steps_per_bench_step": per},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"{per} FV steps of the full {d['nx']}x{d['ny']} grid per bench step"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--tune", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1701_05431_gb300 import fvlib
+
+    build, nsteps_job, desc = WORKLOADS[args.workload]
+    prim, d = build()
+    system = d["system"]
+    nvar = BYTES_PER_CELL[system]
+    ncell = d["nx"] * d["ny"]
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    prim_dev = torch.from_numpy(prim).to(f"cuda:{local}")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def time_jobs(precision, steps, warmup, clocks=False):
+        s = fvlib.Solver(d, precision, stream=sptr, tune=args.tune)
+        s.set_state(prim_dev, primitive=True)
+        for _ in range(warmup):
+            s.run(nsteps_job)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ck = Clocks(local) if clocks else None
+        barrier()
+        if ck:
+            ck.start()
+        ev0.record(stream)
+        for _ in range(steps):
+            s.run(nsteps_job)
+        ev1.record(stream)
+        barrier()
+        ck_res = ck.stop() if ck else None
+        ms = ev0.elapsed_time(ev1)
+        if ws > 1:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        info = s.kernel_info()[1]
+        s.close()
+        return ms, ck_res, info
+
+    # ---- FP32-bulk headline
+    ms32, clk, kinfo32 = time_jobs("f32", args.steps, args.warmup, clocks=(rank == 0))
+    launches = args.steps * nsteps_job
+    value32 = ncell * nsteps_job * args.steps * ws / (ms32 / 1e3)
+    hbm, peak_kind = peaks()
+    algo_bytes_32 = 2 * nvar * 4 * ncell          # one read + one write per cell
+    avg_launch_s = ms32 / 1e3 / launches
+    achieved32 = algo_bytes_32 / avg_launch_s / 1e9
+
+    out = {"metric": "cell-updates/s (FP32-bulk; FP64 plain beside it) and HBM GB/s",
+           "value": value32, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": desc, "cells": ncell, "time_steps_per_bench_step": nsteps_job,
+                      "kernel": kinfo32, "l2": "inputs larger than L2 (state buffers 1 GiB f32 / 2 GiB f64)",
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved32 / hbm, "traffic": None,
+                        "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                        "algorithmic_bytes_per_launch": algo_bytes_32,
+                        "avg_launch_us": avg_launch_s * 1e6},
+           "gpu_launches": launches}
+    if clk:
+        out["clocks"] = clk
+
+    # ---- FP64 plain beside it
+    if not args.no_fp64:
+        k64 = max(1, min(args.steps, 2))
+        ms64, _, kinfo64 = time_jobs("f64", k64, 1)
+        value64 = ncell * nsteps_job * k64 * ws / (ms64 / 1e3)
+        algo64 = 2 * nvar * 8 * ncell
+        avg64 = ms64 / 1e3 / (k64 * nsteps_job)
+        out["fp64"] = {"value": value64, "unit": "cell-updates/s", "ms_per_step": ms64 / k64,
+                       "steps": k64, "kernel": kinfo64,
+                       "hbm_gbs_achieved": algo64 / avg64 / 1e9, "hbm_frac": algo64 / avg64 / 1e9 / hbm,
+                       "note": "FP64 arithmetic is bound by the FP64 pipe, not HBM"}
+        out["fp32_speedup_vs_fp64"] = value32 / value64
+        out["gpu_launches"] += k64 * nsteps_job
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        s = fvlib.Solver(d, "f32", stream=sptr, tune=args.tune)
+        P0 = np.ascontiguousarray(prim.astype(np.float32))
+        h_in = torch.from_numpy(P0).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        s.set_state(h_in, primitive=True)
+        s.run(nsteps_job)
+        s.get_state(h_out)
+        k = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(k):
+            s.set_state(h_in, primitive=True)
+            s.run(nsteps_job)
+            s.get_state(h_out)
+        ev1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = ev0.elapsed_time(ev1)
+        s.close()
+        out["e2e"] = {"value": ncell * nsteps_job * k * ws / (ms / 1e3), "unit": "cell-updates/s",
+                      "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4),
+                      "wall_s": wall, "steps": k,
+                      "path": "fv_set_state(pinned host f32 primitive) + fv_run + fv_get_state(pinned host f32)"}
+        out["gpu_launches"] += k * (nsteps_job + 2)
+
+    # ---- accuracy of the timed configuration against stored oracle samples
+    golden = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle_samples.npz")
+    if os.path.exists(golden):
+        g = np.load(golden)
+        acc = {}
+        for precision in ("f32", "f64"):
+            s = fvlib.Solver(d, precision, stream=sptr)
+            s.set_state(prim_dev, primitive=True)
+            s.run(int(g["steps"]))
+            W = s.state()
+            s.close()
+            idx = g["flat_index"]
+            got = W.reshape(W.shape[0], -1)[:, idx]
+            ref = g["W"]
+            l1 = (np.abs(got - ref).sum(axis=1) / np.abs(ref).sum(axis=1)).tolist()
+            linf = (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).tolist()
+            acc[precision] = {"rel_l1": l1, "rel_linf": linf}
+        out["accuracy_vs_oracle"] = dict(acc, samples=int(len(g["flat_index"])), steps=int(g["steps"]))
+
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline_run(args.workload, d, prim)
+
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

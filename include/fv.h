@@ -1,0 +1,175 @@
+/*
+ * fv.h -- C ABI of the GB300 finite-volume library.
+ *
+ * One explicit first-order finite-volume time step on a 2D Cartesian grid,
+ * as defined in Essadki et al., "A task-driven implementation of a simple
+ * numerical solver for hyperbolic conservation laws" (arXiv:1701.05431):
+ *   - problem statement: Sec. 2.1, Eq. (conservation_law) and
+ *     Eq. (initial_condition): dW/dt + div F(W) = S(W), W in R^nVar;
+ *   - mesh: Sec. 2.2, Nx x Ny cells on [xmin,xmax] x [ymin,ymax];
+ *   - scheme: Sec. 2.2.1, Eq. (VF_scheme) with the Lax-Friedrichs flux and
+ *     the stability condition Eq. (CFL_cond);
+ *   - source: Sec. 2.2.2, Eq. (SourceTerm), first-order splitting;
+ *   - partition: Sec. 3.2 (NPartX x NPartY balanced subdomains) and the
+ *     overlap strips of Sec. 4.1.2;
+ *   - systems: scalar advection; the Euler system of Sec. 5, Eq. (Euler);
+ *     the evaporating-spray moment system of Sec. 6.1, Eq. (Essadki).
+ *
+ * Every step of the method runs in CUDA kernels on one GPU (sm_103a).  All
+ * functions return an fv_status; none throws, exits or aborts.  Functions
+ * taking a context are not thread-safe for the same context.
+ *
+ * Memory layout of every state array crossing this ABI: nVar planes, each
+ * of Ny rows of Nx values, x fastest (var v of cell (i,j) at
+ * v*Nx*Ny + j*Nx + i).  Cell (i,j) is centred at
+ * (xmin + (i+1/2) dx, ymin + (j+1/2) dy).
+ */
+#ifndef FV_H
+#define FV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fv_status {
+  FV_OK = 0,
+  FV_ERR_INVALID_ARG = 1, /* bad argument or configuration                  */
+  FV_ERR_CUDA = 2,        /* a CUDA runtime call failed (see fv_last_error) */
+  FV_ERR_OOM = 3,         /* device allocation failed                       */
+  FV_ERR_CFL = 4,         /* fixed dt violates Eq. (CFL_cond)               */
+  FV_ERR_NONPHYSICAL = 5, /* rho <= 0, p <= 0, non-realizable moments, NaN  */
+  FV_ERR_TIMEOUT = 6,     /* a bounded device wait ran out                  */
+  FV_ERR_STATE = 7        /* call out of order (e.g. run before set_state)  */
+} fv_status;
+
+/* Systems (nVar in parentheses). */
+enum { FV_ADVECTION = 0 /* (1) */, FV_EULER = 1 /* (4) */, FV_SPRAY = 2 /* (6) */ };
+
+/* Storage and arithmetic precision of the state.
+ *   FV_F64: FP64 storage and FP64 arithmetic;
+ *   FV_F32: FP32 storage and FP32 flux/update arithmetic.
+ * In every precision dt, t and the conservation totals are FP64, and the
+ * spray source's maximum-entropy solve is FP64. */
+enum { FV_F64 = 0, FV_F32 = 1 };
+
+/* Boundary conditions, per side (Sec. 4.2, copyOverlaps):
+ *   periodic: the wrapped neighbour cell (E must pair with W, N with S);
+ *   transmissive: a copy of the border cell itself (zero gradient);
+ *   dirichlet: the prescribed conserved state bc_state[side]. */
+enum { FV_BC_PERIODIC = 0, FV_BC_TRANSMISSIVE = 1, FV_BC_DIRICHLET = 2 };
+enum { FV_SIDE_E = 0, FV_SIDE_N = 1, FV_SIDE_W = 2, FV_SIDE_S = 3 };
+
+/* Variable sets accepted by fv_set_state.
+ *   FV_CONSERVED: W itself;
+ *   FV_PRIMITIVE: advection (u); Euler (rho, u, v, p) with
+ *     rho E = p/(gamma-1) + rho (u^2+v^2)/2; spray (m0, m1/2, m1, m3/2, u, v)
+ *     with momenta m1 u, m1 v. */
+enum { FV_CONSERVED = 0, FV_PRIMITIVE = 1 };
+
+/* Problem statement (Sec. 2.1-2.2, 3.2).
+ *   nx, ny >= 1; 1 <= npart_x <= nx, 1 <= npart_y <= ny (balanced split,
+ *     the first Nx mod NPartX parts one cell wider); on one GPU the
+ *     partition is realised as a tile work-list and does not change results.
+ *   params: advection (a_x, a_y); Euler (gamma); spray (K, theta, gas field
+ *     0: at rest / 1: Taylor-Green (sin 2pi x cos 2pi y, -cos 2pi x sin 2pi y),
+ *     Q quadrature nodes (0 -> 32), Newton tolerance (0 -> 1e-13));
+ *     theta <= 0 disables the drag term.
+ *   cfl > 0 and fixed_dt <= 0: adaptive dt_n = cfl min(dx,dy)/lmax(W^n);
+ *   fixed_dt > 0: the paper's constant dt, checked against Eq. (CFL_cond)
+ *     at the start of every step (FV_ERR_CFL on violation).
+ *   stream: cudaStream_t on which all work is queued (NULL: legacy stream).
+ *   tune: 0 = stored kernel choice, 1 = time the candidates at the first
+ *     run and keep the fastest, >= 2: force candidate (tune - 2). */
+typedef struct fv_config {
+  int nx, ny, npart_x, npart_y;
+  double xmin, xmax, ymin, ymax;
+  int system;
+  int precision;
+  int bc[4];
+  double bc_state[4][8];
+  double cfl;
+  double fixed_dt;
+  double params[8];
+  void *stream;
+  int tune;
+} fv_config;
+
+typedef struct fv_ctx fv_ctx;
+
+/* Static text for a status code. */
+const char *fv_status_string(fv_status s);
+
+/* Detail of the last failure on this context ("" if none; ctx may be NULL
+ * for failures of fv_init). Owned by the library. */
+const char *fv_last_error(const fv_ctx *ctx);
+
+/* Validate cfg and allocate every device buffer (two state buffers of
+ * nVar x Ny x pitch values, a control block).  *out receives the context,
+ * owned by the caller until fv_destroy.  FV_ERR_INVALID_ARG for a bad
+ * configuration (unpaired periodic sides, non-positive sizes, unknown
+ * system or precision), FV_ERR_OOM when allocation fails. */
+fv_status fv_init(const fv_config *cfg, fv_ctx **out);
+
+/* Release every device buffer and the context.  NULL is accepted. */
+void fv_destroy(fv_ctx *ctx);
+
+/* Load the state at t = 0, step 0 (initial condition,
+ * Eq. (initial_condition)).  src: nVar x Ny x Nx values (layout above) of
+ * type src_dtype (FV_F64 or FV_F32), on the device when src_is_device != 0
+ * (any device pointer readable on the context's stream) else in host memory
+ * (pinned or pageable).  The caller keeps ownership; the library copies.
+ * Recomputes lmax(W^0) on the device.  Returns FV_ERR_NONPHYSICAL when the
+ * state has rho <= 0, p <= 0, non-finite values or non-realizable moments,
+ * and FV_ERR_INVALID_ARG when adaptive dt meets lmax = 0.  Synchronises the
+ * stream. */
+fv_status fv_set_state(fv_ctx *ctx, const void *src, int src_is_device, int src_dtype,
+                       int layout);
+
+/* Advance by one step (Eq. (VF_scheme) then Eq. (SourceTerm)); *dt_used
+ * (nullable) receives the dt taken.  Same errors as fv_run. */
+fv_status fv_step(fv_ctx *ctx, double *dt_used);
+
+/* Advance by up to nsteps steps (one CUDA graph of nsteps fused step
+ * kernels queued on the stream), stopping at t_end when t_end > 0 (the last
+ * dt is clipped to land on t_end).  *t_out (nullable) receives the time
+ * reached.  Error flags raised on the device are read back once at the end
+ * (this synchronises the stream): FV_ERR_CFL (fixed dt too large; state kept
+ * at the last good step), FV_ERR_NONPHYSICAL (the offending state is the
+ * current state), FV_ERR_STATE when no state was set. */
+fv_status fv_run(fv_ctx *ctx, int nsteps, double t_end, double *t_out);
+
+/* Copy the current conserved state out as nVar x Ny x Nx values of
+ * dst_dtype (FV_F64 or FV_F32), to device (dst_is_device != 0) or host
+ * memory owned by the caller.  Synchronises the stream. */
+fv_status fv_get_state(fv_ctx *ctx, void *dst, int dst_is_device, int dst_dtype);
+
+/* Per-variable totals sum_ij W_v dx dy of the current state (nVar doubles
+ * into host memory), FP64 Neumaier-compensated block sums combined in a
+ * fixed order (deterministic).  Synchronises the stream. */
+fv_status fv_totals(fv_ctx *ctx, double *totals);
+
+/* Simulation time and completed step count of the current state. */
+fv_status fv_time(fv_ctx *ctx, double *t, long long *step);
+
+/* Set the time and step counter of the current state (resume from a
+ * checkpoint written with fv_get_state + fv_time). */
+fv_status fv_set_time(fv_ctx *ctx, double t, long long step);
+
+/* lmax(W^n) of the current state: the largest |eigenvalue| over cells and
+ * the two axis normals, the quantity bounded by Eq. (CFL_cond). */
+fv_status fv_lambda_max(fv_ctx *ctx, double *lmax);
+
+/* Kernel variant in use: *variant receives its index, *desc (nullable) a
+ * static description such as "f32 v2 ty32 w4". */
+fv_status fv_kernel_info(fv_ctx *ctx, int *variant, const char **desc);
+
+/* Q-point Gauss-Legendre nodes x[Q] and weights w[Q] on [0,1] used by the
+ * spray source's maximum-entropy quadrature (Sec. 6.2), as computed by the
+ * library on the host.  1 <= Q <= 128. */
+fv_status fv_gauss_legendre(int Q, double *x, double *w);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FV_H */

@@ -1,0 +1,250 @@
+// fv_aux.cu -- auxiliary kernels around the fused step: loading a state
+// (with the primitive -> conserved map of the initial condition,
+// Eq. (initial_condition)), storing it back in a caller's dtype, the seed
+// reduction of lmax(W^0) for the first dt (Eq. (CFL_cond)) and the
+// compensated conservation totals.
+#include <cuda_runtime.h>
+
+#include "fv_device.cuh"
+#include "fv_internal.h"
+
+namespace fv {
+
+// ------------------------------------------------------------------ load
+template <class S>
+static __device__ __forceinline__ double rd(const S *p, long long k) { return (double)p[k]; }
+
+// One thread per cell.  src is contiguous nvar x ny x nx; state is pitched.
+// Primitive -> conserved, in FP64 and in the same operation order as the
+// definition: rho E = p/(gamma - 1) + rho (u u + v v)/2; momenta = rho u, rho v
+// (Euler) or m1 u, m1 v (spray).
+template <class S, class R>
+__global__ void load_state_kernel(int system, const S *__restrict__ src, int primitive,
+                                  R *__restrict__ state, int nx, int ny, long long pitch,
+                                  long long plane, double gamma) {
+  const long long ncell = (long long)nx * ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / nx), i = (int)(k % nx);
+    const long long o = (long long)j * pitch + i;
+    if (system == kAdvection) {
+      state[o] = (R)rd(src, k);
+    } else if (system == kEuler) {
+      double w0 = rd(src, k), w1 = rd(src, ncell + k), w2 = rd(src, 2 * ncell + k),
+             w3 = rd(src, 3 * ncell + k);
+      if (primitive) {
+        const double rho = w0, u = w1, v = w2, p = w3;
+        w1 = __dmul_rn(rho, u);
+        w2 = __dmul_rn(rho, v);
+        const double q = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
+        w3 = __dadd_rn(__ddiv_rn(p, __dsub_rn(gamma, 1.0)), __ddiv_rn(__dmul_rn(rho, q), 2.0));
+      }
+      state[o] = (R)w0;
+      state[plane + o] = (R)w1;
+      state[2 * plane + o] = (R)w2;
+      state[3 * plane + o] = (R)w3;
+    } else {
+      double w[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) w[v] = rd(src, v * ncell + k);
+      if (primitive) {
+        w[4] = __dmul_rn(w[2], w[4]);
+        w[5] = __dmul_rn(w[2], w[5]);
+      }
+#pragma unroll
+      for (int v = 0; v < 6; ++v) state[v * plane + o] = (R)w[v];
+    }
+  }
+}
+
+static int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t launch_load_state(int system, int prec, const void *src, int src_f32, int primitive,
+                              void *state, int nx, int ny, long long pitch, long long plane,
+                              double gamma, cudaStream_t s) {
+  const int th = 256;
+  const int g = grid_for((long long)nx * ny, th);
+  if (prec == 0) {
+    if (src_f32)
+      load_state_kernel<float, double><<<g, th, 0, s>>>(system, (const float *)src, primitive,
+                                                        (double *)state, nx, ny, pitch, plane, gamma);
+    else
+      load_state_kernel<double, double><<<g, th, 0, s>>>(system, (const double *)src, primitive,
+                                                         (double *)state, nx, ny, pitch, plane, gamma);
+  } else {
+    if (src_f32)
+      load_state_kernel<float, float><<<g, th, 0, s>>>(system, (const float *)src, primitive,
+                                                       (float *)state, nx, ny, pitch, plane, gamma);
+    else
+      load_state_kernel<double, float><<<g, th, 0, s>>>(system, (const double *)src, primitive,
+                                                        (float *)state, nx, ny, pitch, plane, gamma);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ store
+template <class R, class D>
+__global__ void store_state_kernel(int nvar, const R *__restrict__ state, D *__restrict__ dst, int nx,
+                                   int ny, long long pitch, long long plane) {
+  const long long ncell = (long long)nx * ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / nx), i = (int)(k % nx);
+    const long long o = (long long)j * pitch + i;
+    for (int v = 0; v < nvar; ++v) dst[v * ncell + k] = (D)state[v * plane + o];
+  }
+}
+
+cudaError_t launch_store_state(int prec, int nvar, const void *state, void *dst, int dst_f32, int nx,
+                               int ny, long long pitch, long long plane, cudaStream_t s) {
+  const int th = 256;
+  const int g = grid_for((long long)nx * ny, th);
+  if (prec == 0) {
+    if (dst_f32)
+      store_state_kernel<double, float><<<g, th, 0, s>>>(nvar, (const double *)state, (float *)dst, nx,
+                                                         ny, pitch, plane);
+    else
+      store_state_kernel<double, double><<<g, th, 0, s>>>(nvar, (const double *)state, (double *)dst,
+                                                          nx, ny, pitch, plane);
+  } else {
+    if (dst_f32)
+      store_state_kernel<float, float><<<g, th, 0, s>>>(nvar, (const float *)state, (float *)dst, nx,
+                                                        ny, pitch, plane);
+    else
+      store_state_kernel<float, double><<<g, th, 0, s>>>(nvar, (const float *)state, (double *)dst, nx,
+                                                         ny, pitch, plane);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ seed lmax
+// lmax(W^0) and admissibility of a freshly loaded state, with the same
+// per-cell function the step kernel applies to every new state.
+template <class Sys, class R>
+__global__ void seed_lambda_kernel(const R *__restrict__ state, int nx, int ny, long long pitch,
+                                   long long plane, SysParams<R> P, Ctrl *ctrl, int slot) {
+  constexpr int NV = Sys::NV;
+  const long long ncell = (long long)nx * ny;
+  double l = 0.0;
+  bool bad = false;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / nx), i = (int)(k % nx);
+    const long long o = (long long)j * pitch + i;
+    R W[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v] = state[v * plane + o];
+    bool b;
+    R lc = Sys::lambda(W, P, b);
+    bad |= b;
+    l = fmax(l, (double)lc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
+  const int anybad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (l > 0.0) atomicMax(&ctrl->lam[slot], lam_bits(l));
+    if (anybad) atomicOr(&ctrl->err_pending, kErrNonphysical);
+  }
+}
+
+cudaError_t launch_seed_lambda(int system, int prec, const void *state, int nx, int ny,
+                               long long pitch, long long plane, double p0, double p1, Ctrl *ctrl,
+                               int slot, cudaStream_t s) {
+  const int th = 256;
+  const int g = grid_for((long long)nx * ny, th);
+  if (prec == 0) {
+    SysParams<double> P{p0, p1};
+    const double *st = (const double *)state;
+    if (system == kAdvection) seed_lambda_kernel<Advection, double><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+    else if (system == kEuler) seed_lambda_kernel<Euler, double><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+    else seed_lambda_kernel<Spray, double><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+  } else {
+    SysParams<float> P{(float)p0, (float)p1};
+    const float *st = (const float *)state;
+    if (system == kAdvection) seed_lambda_kernel<Advection, float><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+    else if (system == kEuler) seed_lambda_kernel<Euler, float><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+    else seed_lambda_kernel<Spray, float><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ totals
+// Neumaier compensated summation: s + c tracks the exact running sum far
+// better than s alone.
+struct Neu {
+  double s, c;
+};
+static __device__ __forceinline__ void neu_add(Neu &a, double x) {
+  const double t = __dadd_rn(a.s, x);
+  if (fabs(a.s) >= fabs(x)) a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(a.s, t), x));
+  else a.c = __dadd_rn(a.c, __dadd_rn(__dsub_rn(x, t), a.s));
+  a.s = t;
+}
+static __device__ __forceinline__ void neu_merge(Neu &a, const Neu &b) {
+  neu_add(a, b.s);
+  a.c = __dadd_rn(a.c, b.c);
+}
+
+constexpr int kTotThreads = 256;
+constexpr int kMaxVar = 8;
+
+int totals_blocks(int ny) { return ny < 1024 ? ny : 1024; }
+
+// Block b sums rows b, b + gridDim.x, ...; within a block, threads stride
+// along x; the block combines its threads in a fixed tree order.
+template <class R>
+__global__ void totals_partial_kernel(int nvar, const R *__restrict__ state, int nx, int ny,
+                                      long long pitch, long long plane, double *partials) {
+  __shared__ Neu sh[kTotThreads];
+  for (int v = 0; v < nvar; ++v) {
+    Neu acc{0.0, 0.0};
+    for (int j = blockIdx.x; j < ny; j += gridDim.x) {
+      const R *row = state + v * plane + (long long)j * pitch;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) neu_add(acc, (double)row[i]);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kTotThreads / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) neu_merge(sh[threadIdx.x], sh[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      partials[2 * (v * gridDim.x + blockIdx.x)] = sh[0].s;
+      partials[2 * (v * gridDim.x + blockIdx.x) + 1] = sh[0].c;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void totals_final_kernel(int nvar, const double *partials, int nblocks, double *out,
+                                    double cell_area) {
+  const int v = threadIdx.x;
+  if (v >= nvar) return;
+  Neu acc{0.0, 0.0};
+  for (int b = 0; b < nblocks; ++b) {
+    Neu p{partials[2 * (v * nblocks + b)], partials[2 * (v * nblocks + b) + 1]};
+    neu_merge(acc, p);
+  }
+  out[v] = __dmul_rn(__dadd_rn(acc.s, acc.c), cell_area);
+}
+
+cudaError_t launch_totals(int prec, int nvar, const void *state, int nx, int ny, long long pitch,
+                          long long plane, double *partials, int nblocks, double *out,
+                          double cell_area, cudaStream_t s) {
+  if (prec == 0)
+    totals_partial_kernel<double><<<nblocks, kTotThreads, 0, s>>>(nvar, (const double *)state, nx, ny,
+                                                                  pitch, plane, partials);
+  else
+    totals_partial_kernel<float><<<nblocks, kTotThreads, 0, s>>>(nvar, (const float *)state, nx, ny,
+                                                                 pitch, plane, partials);
+  totals_final_kernel<<<1, 32, 0, s>>>(nvar, partials, nblocks, out, cell_area);
+  return cudaGetLastError();
+}
+
+}  // namespace fv

@@ -1,0 +1,232 @@
+// fv_device.cuh -- device-side building blocks of the fused finite-volume
+// step (arXiv:1701.05431, Sec. 2.2): explicitly rounded arithmetic, the
+// physical fluxes of the three systems, the Lax-Friedrichs face flux and the
+// control block that carries lmax, dt and t between steps.
+//
+// Every floating-point operation of the flux, face and update arithmetic goes
+// through Ops<R> (explicitly rounded intrinsics), so the compiler never
+// contracts or reorders it: the x and y code paths then round identically,
+// which makes the x<->y transposition of a state commute with the step bit for
+// bit, and any tile shape gives the same bits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fv {
+
+enum : int { kAdvection = 0, kEuler = 1, kSpray = 2 };
+enum : int { kPeriodic = 0, kTransmissive = 1, kDirichlet = 2 };
+enum : int { kE = 0, kN = 1, kW = 2, kS = 3 };
+enum : unsigned { kErrCfl = 1u, kErrNonphysical = 2u, kErrZeroSpeed = 4u, kErrTimeout = 8u };
+
+// Control block in device memory.  Step n reads lmax(W^n) from lam[n % 3]
+// and accumulates lmax(W^{n+1}) into lam[(n+1) % 3]; the last block of step n
+// clears lam[(n+2) % 3] for the step after.  Only that last block writes t,
+// step and err_committed, after every block has read them, so all blocks of
+// one kernel see the same values.
+struct Ctrl {
+  unsigned long long lam[3];  // bit patterns of non-negative doubles
+  double t;
+  double dt_last;
+  double t_end;               // <= 0: no end time
+  long long step;
+  unsigned int blocks_done;
+  unsigned int err_pending;   // raised by any block during a step
+  unsigned int err_committed; // folded in by the step's last block
+  unsigned int pad_;
+};
+
+template <class R> struct Ops;
+
+template <> struct Ops<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+  static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double abs(double a) { return fabs(a); }
+  static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
+  static __device__ __forceinline__ double neg(double a) { return -a; }
+};
+
+template <> struct Ops<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
+  static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ float neg(float a) { return -a; }
+};
+
+// Parameters of the system, in the arithmetic precision.
+template <class R> struct SysParams {
+  R p0, p1;   // advection: a_x, a_y | Euler: gamma, gamma - 1 | spray: unused
+};
+
+// ---------------------------------------------------------------- systems
+// Each system provides, for one cell W:
+//   fluxes(): F(W).(1,0), the largest |eigenvalue| along x, F(W).(0,1) and
+//             the largest |eigenvalue| along y;
+//   lambda(): max of the two (the cell's term of Eq. (CFL_cond)) and whether
+//             the state is admissible.
+
+// Scalar advection, F = a u: eigenvalue a.n.
+struct Advection {
+  static constexpr int NV = 1;
+  template <class R>
+  static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
+                                                R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {
+    using O = Ops<R>;
+    Fx[0] = O::mul(P.p0, W[0]);
+    Fy[0] = O::mul(P.p1, W[0]);
+    sx = O::abs(P.p0);
+    sy = O::abs(P.p1);
+  }
+  template <class R>
+  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, bool &bad) {
+    using O = Ops<R>;
+    R l = O::max(O::abs(P.p0), O::abs(P.p1));
+    bad = !(W[0] == W[0]) || !(O::abs(W[0]) <= (R)3.0e38);
+    return l;
+  }
+};
+
+// Euler, Eq. (Euler): W = (rho, rho u, rho v, rho E),
+// p = (gamma - 1)(rho E - (rho u u + rho v v)/2), c^2 = gamma p / rho,
+// F.x = (rho u, rho u u + p, rho u v, u (rho E + p)), eigenvalues u -+ c, u.
+struct Euler {
+  static constexpr int NV = 4;
+  template <class R>
+  static __device__ __forceinline__ void prims(const R (&W)[NV], const SysParams<R> &P, R &u,
+                                               R &v, R &p, R &c) {
+    using O = Ops<R>;
+    R inv = O::rcp(W[0]);
+    u = O::mul(W[1], inv);
+    v = O::mul(W[2], inv);
+    // kinetic energy: a plain sum of two rounded products keeps x <-> y symmetry
+    R ke = O::mul((R)0.5, O::add(O::mul(W[1], u), O::mul(W[2], v)));
+    p = O::mul(P.p1, O::sub(W[3], ke));
+    c = O::sqrt(O::mul(O::mul(P.p0, p), inv));
+  }
+  template <class R>
+  static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
+                                                R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {
+    using O = Ops<R>;
+    R u, v, p, c;
+    prims(W, P, u, v, p, c);
+    R Ep = O::add(W[3], p);
+    Fx[0] = W[1];
+    Fx[1] = O::fma(W[1], u, p);
+    Fx[2] = O::mul(W[1], v);
+    Fx[3] = O::mul(u, Ep);
+    Fy[0] = W[2];
+    Fy[1] = O::mul(W[2], u);
+    Fy[2] = O::fma(W[2], v, p);
+    Fy[3] = O::mul(v, Ep);
+    sx = O::add(O::abs(u), c);
+    sy = O::add(O::abs(v), c);
+  }
+  template <class R>
+  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, bool &bad) {
+    using O = Ops<R>;
+    R u, v, p, c;
+    prims(W, P, u, v, p, c);
+    R l = O::add(O::max(O::abs(u), O::abs(v)), c);
+    bad = !(W[0] > (R)0) || !(p > (R)0) || !(l <= (R)3.0e38);
+    return l;
+  }
+};
+
+// Spray moments, Eq. (Essadki): W = (m0, m1/2, m1, m3/2, m1 u, m1 v), all
+// transported by u = (m1 u)/m1; every eigenvalue is u.n.
+struct Spray {
+  static constexpr int NV = 6;
+  template <class R>
+  static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
+                                                R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {
+    using O = Ops<R>;
+    R inv = O::rcp(W[2]);
+    R u = O::mul(W[4], inv);
+    R v = O::mul(W[5], inv);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      Fx[k] = O::mul(W[k], u);
+      Fy[k] = O::mul(W[k], v);
+    }
+    sx = O::abs(u);
+    sy = O::abs(v);
+  }
+  template <class R>
+  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, bool &bad) {
+    using O = Ops<R>;
+    R inv = O::rcp(W[2]);
+    R u = O::mul(W[4], inv);
+    R v = O::mul(W[5], inv);
+    R l = O::max(O::abs(u), O::abs(v));
+    bad = !(W[0] > (R)0) || !(W[2] > (R)0) || !(l <= (R)3.0e38);
+    return l;
+  }
+};
+
+// Lax-Friedrichs face flux of Sec. 2.2.1 for one variable:
+// F~ = (F_L + F_R)/2 - (sigma/2)(W_R - W_L), hs = sigma/2.
+template <class R>
+static __device__ __forceinline__ R lf_face(R WL, R FL, R WR, R FR, R hs) {
+  using O = Ops<R>;
+  return O::fma(O::neg(hs), O::sub(WR, WL), O::mul((R)0.5, O::add(FL, FR)));
+}
+
+// Residual and forward-Euler update of Eq. (VF_scheme) for one variable:
+// W + ( -(lx (Fe - Fw)) - (ly (Fn - Fs)) ).
+template <class R>
+static __device__ __forceinline__ R fv_update(R W, R dX, R dY, R lx, R ly) {
+  using O = Ops<R>;
+  return O::add(W, O::sub(O::neg(O::mul(lx, dX)), O::mul(ly, dY)));
+}
+
+static __device__ __forceinline__ unsigned long long lam_bits(double l) {
+  return (unsigned long long)__double_as_longlong(l);
+}
+static __device__ __forceinline__ double lam_value(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
+// Time step of step n from lmax(W^n), Eq. (CFL_cond):
+//   adaptive: dt = cfl * min(dx, dy) / lmax (capped for the spray drag);
+//   fixed:    dt = fixed_dt after checking fixed_dt * lmax <= min(dx, dy);
+//   both clipped to land on t_end.
+// Returns false when the step must not run; *err then holds the reason
+// (0 when the run simply reached t_end or an earlier error is pending).
+struct DtPolicy {
+  double h;         // min(dx, dy)
+  double cfl;
+  double fixed_dt;
+  double dt_cap;    // +inf unless the system caps dt
+};
+
+static __device__ __forceinline__ bool choose_dt(const DtPolicy &pol, const Ctrl &c, double lam,
+                                                 double *dt, unsigned *err) {
+  *err = 0u;
+  if (c.err_committed != 0u) return false;
+  if (c.t_end > 0.0 && c.t >= c.t_end) return false;
+  if (!(lam <= 1.0e300)) { *err = kErrNonphysical; return false; }
+  double d;
+  if (pol.fixed_dt > 0.0) {
+    if (pol.fixed_dt * lam > pol.h) { *err = kErrCfl; return false; }
+    d = pol.fixed_dt;
+  } else {
+    d = lam > 0.0 ? pol.cfl * pol.h / lam : 1.0e308;
+    if (pol.dt_cap < d) d = pol.dt_cap;
+    if (!(d < 1.0e300)) { *err = kErrZeroSpeed; return false; }
+  }
+  if (c.t_end > 0.0 && c.t + d > c.t_end) d = c.t_end - c.t;
+  *dt = d;
+  return true;
+}
+
+}  // namespace fv

@@ -1,0 +1,589 @@
+// fv_host.cu -- C ABI of the finite-volume library (include/fv.h): context,
+// validation, device buffers, kernel choice, the CUDA-graph time loop and
+// error reporting.  Every numerical step runs in the kernels of fv_step*.cu,
+// fv_spray.cu and fv_aux.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fv.h"
+#include "fv_internal.h"
+#include "fv_step.cuh"
+
+namespace fv {
+
+const std::vector<Variant> &all_variants() {
+  static std::vector<Variant> v;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    register_step_advection(v);
+    register_step_euler(v);
+    register_step_spray(v);
+  });
+  return v;
+}
+
+static int nvar_of(int system) {
+  switch (system) {
+    case kAdvection: return 1;
+    case kEuler: return 4;
+    case kSpray: return 6;
+    default: return 0;
+  }
+}
+
+}  // namespace fv
+
+using namespace fv;
+
+struct fv_ctx {
+  fv_config cfg;
+  int nvar = 0;
+  size_t esize = 0;
+  long long pitch = 0, plane = 0;
+  size_t buf_bytes = 0;
+  void *buf[2] = {nullptr, nullptr};
+  Ctrl *ctrl = nullptr;
+  Ctrl *h_ctrl = nullptr;        // pinned mirror
+  double *h_scalar = nullptr;    // pinned scratch for small uploads
+  void *staging = nullptr;
+  size_t staging_bytes = 0;
+  double *partials = nullptr;
+  double *d_totals = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // graph capture needs a non-legacy stream
+  bool has_state = false;
+  int variant = -1;
+  int grid = 0;
+  double dx = 0, dy = 0;
+  std::map<int, cudaGraphExec_t> graphs;
+  std::string err;
+  int device = 0;
+  int sms = 0;
+};
+
+static std::string g_init_error;
+
+static fv_status fail(fv_ctx *c, fv_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_init_error = msg;
+  return s;
+}
+
+static fv_status cuda_fail(fv_ctx *c, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA, m);
+}
+
+#define FV_CUDA(c, call)                                 \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+extern "C" const char *fv_status_string(fv_status s) {
+  switch (s) {
+    case FV_OK: return "ok";
+    case FV_ERR_INVALID_ARG: return "invalid argument";
+    case FV_ERR_CUDA: return "CUDA error";
+    case FV_ERR_OOM: return "out of device memory";
+    case FV_ERR_CFL: return "fixed time step violates the CFL condition";
+    case FV_ERR_NONPHYSICAL: return "non-physical state";
+    case FV_ERR_TIMEOUT: return "device wait timed out";
+    case FV_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+extern "C" const char *fv_last_error(const fv_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+static fv_status validate(const fv_config *c) {
+  if (!c) return fail(nullptr, FV_ERR_INVALID_ARG, "config is NULL");
+  if (nvar_of(c->system) == 0) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown system");
+  if (c->precision != FV_F64 && c->precision != FV_F32)
+    return fail(nullptr, FV_ERR_INVALID_ARG, "unknown precision");
+  if (c->nx < 1 || c->ny < 1) return fail(nullptr, FV_ERR_INVALID_ARG, "nx and ny must be >= 1");
+  if ((long long)c->nx * c->ny > (1LL << 34))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "grid too large");
+  if (c->npart_x < 1 || c->npart_y < 1 || c->npart_x > c->nx || c->npart_y > c->ny)
+    return fail(nullptr, FV_ERR_INVALID_ARG, "need 1 <= npart_x <= nx and 1 <= npart_y <= ny");
+  if (!(c->xmax > c->xmin) || !(c->ymax > c->ymin))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "empty domain");
+  for (int s = 0; s < 4; ++s)
+    if (c->bc[s] < 0 || c->bc[s] > 2) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown boundary condition");
+  if ((c->bc[FV_SIDE_E] == FV_BC_PERIODIC) != (c->bc[FV_SIDE_W] == FV_BC_PERIODIC))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "periodic E must pair with periodic W");
+  if ((c->bc[FV_SIDE_N] == FV_BC_PERIODIC) != (c->bc[FV_SIDE_S] == FV_BC_PERIODIC))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "periodic N must pair with periodic S");
+  if (!(c->fixed_dt > 0.0) && !(c->cfl > 0.0))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "need cfl > 0 or fixed_dt > 0");
+  if (!std::isfinite(c->cfl) || !std::isfinite(c->fixed_dt))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "cfl and fixed_dt must be finite");
+  if (c->system == FV_EULER && !(c->params[0] > 1.0))
+    return fail(nullptr, FV_ERR_INVALID_ARG, "Euler needs gamma > 1");
+  if (c->system == FV_SPRAY) {
+    int Q = (int)c->params[3];
+    if (Q < 0 || Q > 64) return fail(nullptr, FV_ERR_INVALID_ARG, "spray quadrature: 0 <= Q <= 64");
+    if (c->params[0] < 0.0) return fail(nullptr, FV_ERR_INVALID_ARG, "spray K must be >= 0");
+  }
+  return FV_OK;
+}
+
+// Default kernel per (system, precision): the first registered candidate.
+static int default_variant(int system, int prec) {
+  const auto &vs = all_variants();
+  for (size_t k = 0; k < vs.size(); ++k)
+    if (vs[k].system == system && vs[k].precision == prec) return (int)k;
+  return -1;
+}
+
+static std::vector<int> candidates(int system, int prec) {
+  std::vector<int> out;
+  const auto &vs = all_variants();
+  for (size_t k = 0; k < vs.size(); ++k)
+    if (vs[k].system == system && vs[k].precision == prec) out.push_back((int)k);
+  return out;
+}
+
+static void free_graphs(fv_ctx *c) {
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+static fv_status select_variant(fv_ctx *c, int vi) {
+  const Variant &V = all_variants()[vi];
+  int nb = 0;
+  FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, 0));
+  if (nb < 1) return fail(c, FV_ERR_CUDA, std::string("kernel cannot launch: ") + V.desc);
+  const int nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
+  const int nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
+  const long long ntasks = (long long)nstrips * nchunks;
+  long long need = (ntasks + V.NW - 1) / V.NW;
+  long long grid = (long long)nb * c->sms;
+  if (need < grid) grid = need;
+  if (grid < 1) grid = 1;
+  c->variant = vi;
+  c->grid = (int)grid;
+  free_graphs(c);
+  return FV_OK;
+}
+
+template <class R>
+static StepArgs<R> make_args(const fv_ctx *c, const Variant &V) {
+  StepArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.buf0 = (R *)c->buf[0];
+  a.buf1 = (R *)c->buf[1];
+  a.ctrl = c->ctrl;
+  a.nx = c->cfg.nx;
+  a.ny = c->cfg.ny;
+  a.pitch = c->pitch;
+  a.plane = c->plane;
+  a.nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
+  a.nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
+  a.ntasks = a.nstrips * a.nchunks;
+  a.dx = c->dx;
+  a.dy = c->dy;
+  a.pol.h = c->dx < c->dy ? c->dx : c->dy;
+  a.pol.cfl = c->cfg.cfl;
+  a.pol.fixed_dt = c->cfg.fixed_dt;
+  a.pol.dt_cap = 1.0e308;
+  if (c->cfg.system == FV_SPRAY && c->cfg.params[1] > 0.0) a.pol.dt_cap = 0.5 * c->cfg.params[1];
+  if (c->cfg.system == FV_ADVECTION) {
+    a.sp.p0 = (R)c->cfg.params[0];
+    a.sp.p1 = (R)c->cfg.params[1];
+  } else if (c->cfg.system == FV_EULER) {
+    a.sp.p0 = (R)c->cfg.params[0];
+    a.sp.p1 = (R)(c->cfg.params[0] - 1.0);
+  }
+  for (int s = 0; s < 4; ++s) {
+    a.bc[s] = c->cfg.bc[s];
+    for (int v = 0; v < 8; ++v) a.bc_state[s][v] = (R)c->cfg.bc_state[s][v];
+  }
+  a.finalize = c->cfg.system == FV_SPRAY ? 0 : 1;
+  return a;
+}
+
+static fv_status launch_step(fv_ctx *c, cudaStream_t s) {
+  const Variant &V = all_variants()[c->variant];
+  dim3 grid(c->grid), block(V.NW * 32);
+  cudaError_t e;
+  if (V.precision == 0) {
+    StepArgs<double> a = make_args<double>(c, V);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(V.kernel, grid, block, args, 0, s);
+  } else {
+    StepArgs<float> a = make_args<float>(c, V);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(V.kernel, grid, block, args, 0, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+  return FV_OK;
+}
+
+static fv_status get_graph(fv_ctx *c, int nsteps, cudaGraphExec_t *out) {
+  auto it = c->graphs.find(nsteps);
+  if (it != c->graphs.end()) {
+    *out = it->second;
+    return FV_OK;
+  }
+  if (c->graphs.size() > 16) free_graphs(c);
+  FV_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  fv_status st = FV_OK;
+  for (int k = 0; k < nsteps && st == FV_OK; ++k) st = launch_step(c, c->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st != FV_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  c->graphs[nsteps] = ge;
+  *out = ge;
+  return FV_OK;
+}
+
+static fv_status read_ctrl(fv_ctx *c) {
+  FV_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FV_OK;
+}
+
+static fv_status status_of_flags(fv_ctx *c, unsigned e) {
+  if (e & kErrTimeout) return fail(c, FV_ERR_TIMEOUT, "device wait timed out");
+  if (e & kErrCfl) return fail(c, FV_ERR_CFL, "fixed dt * lmax > min(dx, dy)");
+  if (e & kErrNonphysical) return fail(c, FV_ERR_NONPHYSICAL, "non-physical state reached");
+  if (e & kErrZeroSpeed)
+    return fail(c, FV_ERR_INVALID_ARG, "lmax = 0 leaves the adaptive time step unbounded");
+  return FV_OK;
+}
+
+extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
+  if (!out) return fail(nullptr, FV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  fv_status st = validate(cfg);
+  if (st != FV_OK) return st;
+  fv_ctx *c = new fv_ctx();
+  c->cfg = *cfg;
+  c->nvar = nvar_of(cfg->system);
+  c->esize = cfg->precision == FV_F64 ? 8 : 4;
+  // pitch: a multiple of 32 elements (128 B in FP32, 256 B in FP64) so every
+  // row and every V-wide vector access is aligned
+  c->pitch = ((long long)cfg->nx + 31) / 32 * 32;
+  c->plane = c->pitch * cfg->ny;
+  c->buf_bytes = (size_t)c->plane * c->nvar * c->esize;
+  c->dx = (cfg->xmax - cfg->xmin) / cfg->nx;
+  c->dy = (cfg->ymax - cfg->ymin) / cfg->ny;
+  c->stream = (cudaStream_t)cfg->stream;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) {
+    cuda_fail(nullptr, e, "device query");
+    delete c;
+    return FV_ERR_CUDA;
+  }
+  auto bail = [&](cudaError_t e2, const char *what) {
+    cuda_fail(nullptr, e2, what);
+    fv_destroy(c);
+    return e2 == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA;
+  };
+  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(e, "cudaStreamCreate");
+  for (int b = 0; b < 2; ++b)
+    if ((e = cudaMalloc(&c->buf[b], c->buf_bytes)) != cudaSuccess) return bail(e, "cudaMalloc(state)");
+  if ((e = cudaMalloc(&c->ctrl, sizeof(Ctrl))) != cudaSuccess) return bail(e, "cudaMalloc(ctrl)");
+  if ((e = cudaMallocHost(&c->h_ctrl, sizeof(Ctrl))) != cudaSuccess) return bail(e, "cudaMallocHost");
+  if ((e = cudaMallocHost(&c->h_scalar, 64)) != cudaSuccess) return bail(e, "cudaMallocHost");
+  const int nb = totals_blocks(cfg->ny);
+  if ((e = cudaMalloc(&c->partials, sizeof(double) * 2 * 8 * nb)) != cudaSuccess)
+    return bail(e, "cudaMalloc(partials)");
+  if ((e = cudaMalloc(&c->d_totals, sizeof(double) * 8)) != cudaSuccess) return bail(e, "cudaMalloc(totals)");
+  if ((e = cudaMemset(c->ctrl, 0, sizeof(Ctrl))) != cudaSuccess) return bail(e, "cudaMemset");
+  int prec = cfg->precision == FV_F64 ? 0 : 1;
+  int vi = default_variant(cfg->system, prec);
+  if (cfg->tune >= 2) {
+    auto cand = candidates(cfg->system, prec);
+    if (cfg->tune - 2 >= (int)cand.size()) {
+      fv_destroy(c);
+      return fail(nullptr, FV_ERR_INVALID_ARG, "tune index out of range");
+    }
+    vi = cand[cfg->tune - 2];
+  }
+  if (vi < 0) {
+    fv_destroy(c);
+    return fail(nullptr, FV_ERR_INVALID_ARG, "no kernel built for this system and precision");
+  }
+  st = select_variant(c, vi);
+  if (st != FV_OK) {
+    g_init_error = c->err;
+    fv_destroy(c);
+    return st;
+  }
+  *out = c;
+  return FV_OK;
+}
+
+extern "C" void fv_destroy(fv_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_graphs(c);
+  for (int b = 0; b < 2; ++b)
+    if (c->buf[b]) cudaFree(c->buf[b]);
+  if (c->ctrl) cudaFree(c->ctrl);
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->h_scalar) cudaFreeHost(c->h_scalar);
+  if (c->staging) cudaFree(c->staging);
+  if (c->partials) cudaFree(c->partials);
+  if (c->d_totals) cudaFree(c->d_totals);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+static fv_status ensure_staging(fv_ctx *c, size_t bytes) {
+  if (c->staging_bytes >= bytes) return FV_OK;
+  if (c->staging) {
+    FV_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->staging);
+    c->staging = nullptr;
+    c->staging_bytes = 0;
+  }
+  FV_CUDA(c, cudaMalloc(&c->staging, bytes));
+  c->staging_bytes = bytes;
+  return FV_OK;
+}
+
+// Recompute lmax of the current state into slot `step % 3`, clear the other
+// slots and report an inadmissible state.
+static fv_status seed(fv_ctx *c, long long step, double t) {
+  Ctrl h;
+  std::memset(&h, 0, sizeof(h));
+  h.step = step;
+  h.t = t;
+  *c->h_ctrl = h;
+  FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+  const int cur = c->cfg.system == FV_EULER ? 0 : 0;
+  (void)cur;
+  double p0 = c->cfg.params[0], p1 = c->cfg.params[1];
+  if (c->cfg.system == FV_EULER) p1 = c->cfg.params[0] - 1.0;
+  FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision == FV_F64 ? 0 : 1, c->buf[step & 1],
+                                c->cfg.nx, c->cfg.ny, c->pitch, c->plane, p0, p1, c->ctrl,
+                                (int)(step % 3), c->stream));
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  unsigned bad = c->h_ctrl->err_pending;
+  if (bad) {
+    // keep nothing: clear the flag so a corrected state can be loaded later
+    c->h_ctrl->err_pending = 0;
+    FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+    FV_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->has_state = false;
+    return fail(c, FV_ERR_NONPHYSICAL, "state has rho <= 0, p <= 0, non-finite or non-realizable values");
+  }
+  c->has_state = true;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_set_state(fv_ctx *c, const void *src, int src_is_device, int src_dtype,
+                                  int layout) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!src) return fail(c, FV_ERR_INVALID_ARG, "src is NULL");
+  if (src_dtype != FV_F64 && src_dtype != FV_F32) return fail(c, FV_ERR_INVALID_ARG, "bad src_dtype");
+  if (layout != FV_CONSERVED && layout != FV_PRIMITIVE) return fail(c, FV_ERR_INVALID_ARG, "bad layout");
+  const long long ncell = (long long)c->cfg.nx * c->cfg.ny;
+  const size_t sbytes = (size_t)ncell * c->nvar * (src_dtype == FV_F64 ? 8 : 4);
+  const void *dsrc = src;
+  if (!src_is_device) {
+    fv_status st = ensure_staging(c, sbytes);
+    if (st != FV_OK) return st;
+    FV_CUDA(c, cudaMemcpyAsync(c->staging, src, sbytes, cudaMemcpyHostToDevice, c->stream));
+    dsrc = c->staging;
+  }
+  const int prec = c->cfg.precision == FV_F64 ? 0 : 1;
+  FV_CUDA(c, launch_load_state(c->cfg.system, prec, dsrc, src_dtype == FV_F32, layout == FV_PRIMITIVE,
+                               c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->cfg.params[0],
+                               c->stream));
+  return seed(c, 0, 0.0);
+}
+
+extern "C" fv_status fv_get_state(fv_ctx *c, void *dst, int dst_is_device, int dst_dtype) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!dst) return fail(c, FV_ERR_INVALID_ARG, "dst is NULL");
+  if (dst_dtype != FV_F64 && dst_dtype != FV_F32) return fail(c, FV_ERR_INVALID_ARG, "bad dst_dtype");
+  if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  const void *cur = c->buf[c->h_ctrl->step & 1];
+  const int prec = c->cfg.precision == FV_F64 ? 0 : 1;
+  const size_t dsz = dst_dtype == FV_F64 ? 8 : 4;
+  const bool same = (dst_dtype == FV_F64) == (prec == 0);
+  const long long ncell = (long long)c->cfg.nx * c->cfg.ny;
+  if (same) {
+    // planes are contiguous at stride ny * pitch: one 2D copy of nvar * ny rows
+    FV_CUDA(c, cudaMemcpy2DAsync(dst, c->cfg.nx * dsz, cur, c->pitch * c->esize, c->cfg.nx * dsz,
+                                 (size_t)c->nvar * c->cfg.ny,
+                                 dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c->stream));
+  } else {
+    void *target = dst;
+    if (!dst_is_device) {
+      st = ensure_staging(c, (size_t)ncell * c->nvar * dsz);
+      if (st != FV_OK) return st;
+      target = c->staging;
+    }
+    FV_CUDA(c, launch_store_state(prec, c->nvar, cur, target, dst_dtype == FV_F32, c->cfg.nx, c->cfg.ny,
+                                  c->pitch, c->plane, c->stream));
+    if (!dst_is_device)
+      FV_CUDA(c, cudaMemcpyAsync(dst, c->staging, (size_t)ncell * c->nvar * dsz, cudaMemcpyDeviceToHost,
+                                 c->stream));
+  }
+  FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FV_OK;
+}
+
+extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (nsteps < 0) return fail(c, FV_ERR_INVALID_ARG, "nsteps < 0");
+  if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
+  if (!std::isfinite(t_end)) return fail(c, FV_ERR_INVALID_ARG, "t_end must be finite");
+  *c->h_scalar = t_end;
+  FV_CUDA(c, cudaMemcpyAsync(&c->ctrl->t_end, c->h_scalar, sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+  const int chunk = 64;
+  int left = nsteps;
+  while (left > 0) {
+    const int n = left >= chunk ? chunk : left;
+    cudaGraphExec_t g;
+    fv_status st = get_graph(c, n, &g);
+    if (st != FV_OK) return st;
+    FV_CUDA(c, cudaGraphLaunch(g, c->stream));
+    left -= n;
+  }
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  if (t_out) *t_out = c->h_ctrl->t;
+  return status_of_flags(c, c->h_ctrl->err_committed);
+}
+
+extern "C" fv_status fv_step(fv_ctx *c, double *dt_used) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  const long long before = c->h_ctrl->step;
+  st = fv_run(c, 1, 0.0, nullptr);
+  if (dt_used) *dt_used = c->h_ctrl->step > before ? c->h_ctrl->dt_last : 0.0;
+  return st;
+}
+
+extern "C" fv_status fv_totals(fv_ctx *c, double *totals) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!totals) return fail(c, FV_ERR_INVALID_ARG, "totals is NULL");
+  if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  const int nb = totals_blocks(c->cfg.ny);
+  FV_CUDA(c, launch_totals(c->cfg.precision == FV_F64 ? 0 : 1, c->nvar, c->buf[c->h_ctrl->step & 1],
+                           c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->partials, nb, c->d_totals,
+                           c->dx * c->dy, c->stream));
+  FV_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_totals, sizeof(double) * c->nvar, cudaMemcpyDeviceToHost,
+                             c->stream));
+  FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int v = 0; v < c->nvar; ++v) totals[v] = c->h_scalar[v];
+  return FV_OK;
+}
+
+extern "C" fv_status fv_time(fv_ctx *c, double *t, long long *step) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  if (t) *t = c->h_ctrl->t;
+  if (step) *step = c->h_ctrl->step;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_set_time(fv_ctx *c, double t, long long step) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
+  if (step < 0 || !std::isfinite(t)) return fail(c, FV_ERR_INVALID_ARG, "bad time or step");
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  const long long cur = c->h_ctrl->step;
+  if ((cur & 1) != (step & 1)) {
+    // the state lives in buffer step % 2: move it to the new parity
+    FV_CUDA(c, cudaMemcpyAsync(c->buf[step & 1], c->buf[cur & 1], c->buf_bytes, cudaMemcpyDeviceToDevice,
+                               c->stream));
+  }
+  return seed(c, step, t);
+}
+
+extern "C" fv_status fv_lambda_max(fv_ctx *c, double *lmax) {
+  if (!c || !lmax) return FV_ERR_INVALID_ARG;
+  if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  *lmax = __builtin_bit_cast(double, c->h_ctrl->lam[c->h_ctrl->step % 3]);
+  return FV_OK;
+}
+
+extern "C" fv_status fv_kernel_info(fv_ctx *c, int *variant, const char **desc) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  const Variant &V = all_variants()[c->variant];
+  if (variant) {
+    auto cand = candidates(V.system, V.precision);
+    int idx = 0;
+    for (size_t k = 0; k < cand.size(); ++k)
+      if (cand[k] == c->variant) idx = (int)k;
+    *variant = idx;
+  }
+  if (desc) *desc = V.desc;
+  return FV_OK;
+}
+
+// Gauss-Legendre rule on [0,1]: roots of P_Q by Newton's method on the
+// three-term recurrence, weights 2/((1 - t^2) P_Q'(t)^2) halved for [0,1].
+extern "C" fv_status fv_gauss_legendre(int Q, double *x, double *w) {
+  if (Q < 1 || Q > 128 || !x || !w) return FV_ERR_INVALID_ARG;
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < Q; ++i) {
+    double t = std::cos(pi * (4.0 * i + 3.0) / (4.0 * Q + 2.0));
+    double pq = 0, pq1 = 0;
+    for (int it = 0; it < 100; ++it) {
+      double a = 1.0, b = t;  // P_0, P_1
+      for (int k = 2; k <= Q; ++k) {
+        double nxt = ((2.0 * k - 1.0) * t * b - (k - 1.0) * a) / k;
+        a = b;
+        b = nxt;
+      }
+      pq = Q == 0 ? 1.0 : b;
+      pq1 = Q == 1 ? 1.0 : a;
+      const double d = Q * (pq1 - t * pq) / (1.0 - t * t);  // P_Q'
+      const double step = pq / d;
+      t -= step;
+      if (std::fabs(step) <= 1e-16 * std::fabs(t) + 1e-300) break;
+    }
+    double a = 1.0, b = t;
+    for (int k = 2; k <= Q; ++k) {
+      double nxt = ((2.0 * k - 1.0) * t * b - (k - 1.0) * a) / k;
+      a = b;
+      b = nxt;
+    }
+    pq1 = Q == 1 ? 1.0 : a;
+    pq = b;
+    const double d = Q * (pq1 - t * pq) / (1.0 - t * t);
+    x[Q - 1 - i] = 0.5 * (1.0 + t);
+    w[Q - 1 - i] = 1.0 / ((1.0 - t * t) * d * d);
+  }
+  return FV_OK;
+}

@@ -1,0 +1,48 @@
+// fv_internal.h -- host-side declarations shared by the library's translation
+// units (kernel variant registry and auxiliary kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "fv_device.cuh"
+
+namespace fv {
+
+// One compiled step-kernel candidate.
+struct Variant {
+  int system;      // kAdvection / kEuler / kSpray
+  int precision;   // 0: f64, 1: f32
+  int V;           // cells per lane along x
+  int TY;          // rows per warp task
+  int NW;          // warps per block
+  const void *kernel;
+  const char *desc;
+};
+
+// Registration hooks, one per translation unit of step kernels.
+void register_step_advection(std::vector<Variant> &out);
+void register_step_euler(std::vector<Variant> &out);
+void register_step_spray(std::vector<Variant> &out);
+
+const std::vector<Variant> &all_variants();
+
+// Auxiliary kernels (fv_aux.cu).  `R` storage precision: 0 f64, 1 f32.
+cudaError_t launch_load_state(int system, int prec, const void *src, int src_f32, int primitive,
+                              void *state, int nx, int ny, long long pitch, long long plane,
+                              double gamma, cudaStream_t s);
+cudaError_t launch_store_state(int prec, int nvar, const void *state, void *dst, int dst_f32, int nx,
+                               int ny, long long pitch, long long plane, cudaStream_t s);
+cudaError_t launch_seed_lambda(int system, int prec, const void *state, int nx, int ny,
+                               long long pitch, long long plane, double p0, double p1, Ctrl *ctrl,
+                               int slot, cudaStream_t s);
+cudaError_t launch_totals(int prec, int nvar, const void *state, int nx, int ny, long long pitch,
+                          long long plane, double *partials, int nblocks, double *out,
+                          double cell_area, cudaStream_t s);
+int totals_blocks(int ny);
+
+// Spray source step (fv_spray.cu).
+struct SprayArgs;
+
+}  // namespace fv

@@ -54,13 +54,18 @@ def problem(system: str, nx: int, ny: int, **kw) -> dict:
 
 
 def _sin_sum(x, y, terms, amp):
-    """amp * sum_k sin(2 pi (kx x + ky y) + phi) on the grid, separable form."""
-    out = np.zeros((len(y), len(x)))
+    """amp * sum_k sin(2 pi (kx x + ky y) + phi) on the grid, evaluated in the
+    separable form sin(a + b) = cos b sin a + sin b cos a as one small matrix
+    product (rows: y factors, columns: x factors)."""
+    cols_y, cols_x = [], []
     for kx, ky, phi in terms:
         a = 2.0 * math.pi * kx * x + phi
         b = 2.0 * math.pi * ky * y
-        out += np.outer(np.cos(b), np.sin(a)) + np.outer(np.sin(b), np.cos(a))
-    return amp * out
+        cols_y += [np.cos(b), np.sin(b)]
+        cols_x += [np.sin(a), np.cos(a)]
+    Y = np.stack(cols_y, axis=1)
+    X = np.stack(cols_x, axis=0)
+    return amp * (Y @ X)
 
 
 # ---------------------------------------------------------------- advection
