@@ -48,6 +48,8 @@ WORKLOADS = {
     # name: (builder, steps per job, description)
     "c3": (lambda: wl.smooth_periodic(8192), 100,
            "euler 8192x8192 periodic smooth sinusoids, CFL 0.4, 100 steps"),
+    "c3s": (lambda: wl.smooth_periodic(4096), 100,
+            "euler 4096x4096 periodic smooth sinusoids, CFL 0.4, 100 steps (profiling size)"),
     "c2": (lambda: wl.four_quadrant(2048, npart=8), 500,
            "euler 2048x2048 four-quadrant Riemann, 8x8 subdomains, transmissive, CFL 0.4, 500 steps"),
     "c1": (lambda: wl.advection_bump(128), 100,
@@ -74,7 +76,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -191,6 +193,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--tune", type=int, default=0)
+    ap.add_argument("--only", choices=["f32", "f64"], default=None,
+                    help="time one precision only (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -244,6 +248,13 @@ def main():
         s.close()
         return ms, ck_res, info
 
+    if args.only == "f64":
+        ms, _, kinfo = time_jobs("f64", args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"profile_only": "f64", "kernel": kinfo, "ms_per_step": ms / args.steps,
+                              "value": ncell * nsteps_job * args.steps / (ms / 1e3)}))
+        return 0
+
     # ---- FP32-bulk headline
     ms32, clk, kinfo32 = time_jobs("f32", args.steps, args.warmup, clocks=(rank == 0))
     launches = args.steps * nsteps_job
@@ -270,6 +281,8 @@ def main():
         out["clocks"] = clk
 
     # ---- FP64 plain beside it
+    if args.only == "f32":
+        args.no_fp64 = args.no_e2e = args.no_cpu_baseline = True
     if not args.no_fp64:
         k64 = max(1, min(args.steps, 2))
         ms64, _, kinfo64 = time_jobs("f64", k64, 1)

@@ -163,6 +163,13 @@ fv_status fv_lambda_max(fv_ctx *ctx, double *lmax);
  * static description such as "f32 v2 ty32 w4". */
 fv_status fv_kernel_info(fv_ctx *ctx, int *variant, const char **desc);
 
+/* Description of compiled kernel candidate `index` (0-based) for a system
+ * and precision, e.g. "euler f32 v1 ty64 w4 b6": V cells per lane, TY rows
+ * per warp task, NW warps per block, register budget for b blocks per SM.
+ * FV_ERR_INVALID_ARG past the last candidate.  fv_config.tune = index + 2
+ * forces that candidate; tune = 1 times them all on the first fv_run. */
+fv_status fv_kernel_candidate(int system, int precision, int index, const char **desc);
+
 /* Q-point Gauss-Legendre nodes x[Q] and weights w[Q] on [0,1] used by the
  * spray source's maximum-entropy quadrature (Sec. 6.2), as computed by the
  * library on the host.  1 <= Q <= 128. */

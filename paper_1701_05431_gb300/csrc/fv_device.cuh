@@ -56,8 +56,19 @@ template <> struct Ops<float> {
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-  static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
-  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+  // FP32 reciprocal and square root use the single-instruction approximations
+  // of the special-function unit (relative error of a few ulp); FP32 results
+  // are held to a 1e-5 relative L1 bound against the FP64 oracle, far above it.
+  static __device__ __forceinline__ float rcp(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+  }
+  static __device__ __forceinline__ float sqrt(float a) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+  }
   static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
   static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
   static __device__ __forceinline__ float neg(float a) { return -a; }
@@ -168,7 +179,13 @@ struct Spray {
     R u = O::mul(W[4], inv);
     R v = O::mul(W[5], inv);
     R l = O::max(O::abs(u), O::abs(v));
-    bad = !(W[0] > (R)0) || !(W[2] > (R)0) || !(l <= (R)3.0e38);
+    // moments (m0, m1/2, m1, m3/2) strictly inside the moment space of
+    // measures on [0,1]: positive Hankel determinants (checked in FP64)
+    const double c0 = W[0], c1 = W[1], c2 = W[2], c3 = W[3];
+    const bool inside = c0 > 0.0 && c1 > 0.0 && c0 - c1 > 0.0 && c0 * c2 - c1 * c1 > 0.0 &&
+                        c1 - c2 > 0.0 && c1 * c3 - c2 * c2 > 0.0 &&
+                        (c0 - c1) * (c2 - c3) - (c1 - c2) * (c1 - c2) > 0.0;
+    bad = !inside || !(l <= (R)3.0e38);
     return l;
   }
 };
@@ -227,6 +244,78 @@ static __device__ __forceinline__ bool choose_dt(const DtPolicy &pol, const Ctrl
   if (c.t_end > 0.0 && c.t + d > c.t_end) d = c.t_end - c.t;
   *dt = d;
   return true;
+}
+
+// Every step kernel starts by reading the control block once (thread 0) and
+// deciding whether the step runs and with which dt.
+struct StepStart {
+  double dt;
+  long long step;
+  unsigned err;
+  int run;
+};
+
+static __device__ __forceinline__ StepStart read_step_start(const DtPolicy &pol, Ctrl *ctrl) {
+  Ctrl c;
+  c.step = __ldcg(&ctrl->step);
+  c.t = __ldcg(&ctrl->t);
+  c.t_end = __ldcg(&ctrl->t_end);
+  c.err_committed = __ldcg(&ctrl->err_committed);
+  const double lam = lam_value(__ldcg(&ctrl->lam[c.step % 3]));
+  StepStart s;
+  s.dt = 0.0;
+  s.step = c.step;
+  s.run = choose_dt(pol, c, lam, &s.dt, &s.err) ? 1 : 0;
+  return s;
+}
+
+// Close a step: reduce lmax(W^{n+1}) and the admissibility flag over the
+// block (warp shuffles, then one shared slot per warp), fold them into the
+// control block with one atomic each, and let the last block to finish
+// advance t and n, clear the lmax slot of step n + 2 and commit the error
+// flags.  Must be reached by every thread of every block.
+template <int NW>
+static __device__ __forceinline__ void finish_step(Ctrl *ctrl, const StepStart &st, double lam,
+                                                   bool bad, double *s_lam, int *s_bad) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  const int anybad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    s_lam[warp] = lam;
+    s_bad[warp] = anybad;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double bl = 0.0;
+  int bb = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    bl = fmax(bl, s_lam[w]);
+    bb |= s_bad[w];
+  }
+  const long long n = st.step;
+  if (st.run) {
+    // an inadmissible state poisons the slot with a NaN so the next dt fails too
+    if (bb) atomicMax(&ctrl->lam[(n + 1) % 3], 0x7ff8000000000000ull);
+    else if (bl > 0.0) atomicMax(&ctrl->lam[(n + 1) % 3], lam_bits(bl));
+    if (bb) atomicOr(&ctrl->err_pending, kErrNonphysical);
+  }
+  __threadfence();
+  const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
+  if (prev == gridDim.x - 1) {
+    __threadfence();
+    ctrl->blocks_done = 0u;
+    const unsigned e = atomicExch(&ctrl->err_pending, 0u) | st.err;
+    if (st.run) {
+      ctrl->t = ctrl->t + st.dt;
+      ctrl->dt_last = st.dt;
+      ctrl->step = n + 1;
+      ctrl->lam[(n + 2) % 3] = 0ull;
+    }
+    if (e) ctrl->err_committed |= e;
+    __threadfence();
+  }
 }
 
 }  // namespace fv

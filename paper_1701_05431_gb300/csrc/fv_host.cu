@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -56,6 +57,10 @@ struct fv_ctx {
   size_t staging_bytes = 0;
   double *partials = nullptr;
   double *d_totals = nullptr;
+  double *lamw = nullptr;        // spray: warm-start multipliers (4 planes)
+  double *nodes = nullptr;       // spray: quadrature table
+  int spray_Q = 0;
+  int src_grid = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // graph capture needs a non-legacy stream
   bool has_state = false;
@@ -66,6 +71,7 @@ struct fv_ctx {
   std::string err;
   int device = 0;
   int sms = 0;
+  bool tuned = false;
 };
 
 static std::string g_init_error;
@@ -208,7 +214,6 @@ static StepArgs<R> make_args(const fv_ctx *c, const Variant &V) {
     a.bc[s] = c->cfg.bc[s];
     for (int v = 0; v < 8; ++v) a.bc_state[s][v] = (R)c->cfg.bc_state[s][v];
   }
-  a.finalize = c->cfg.system == FV_SPRAY ? 0 : 1;
   return a;
 }
 
@@ -216,16 +221,45 @@ static fv_status launch_step(fv_ctx *c, cudaStream_t s) {
   const Variant &V = all_variants()[c->variant];
   dim3 grid(c->grid), block(V.NW * 32);
   cudaError_t e;
+  DtPolicy pol;
   if (V.precision == 0) {
     StepArgs<double> a = make_args<double>(c, V);
+    pol = a.pol;
     void *args[] = {&a};
     e = cudaLaunchKernel(V.kernel, grid, block, args, 0, s);
   } else {
     StepArgs<float> a = make_args<float>(c, V);
+    pol = a.pol;
     void *args[] = {&a};
     e = cudaLaunchKernel(V.kernel, grid, block, args, 0, s);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+  if (c->cfg.system == FV_SPRAY) {
+    // split source step, Eq. (SourceTerm); it closes the step
+    SourceLaunch L;
+    L.prec = V.precision;
+    L.buf0 = c->buf[0];
+    L.buf1 = c->buf[1];
+    L.ctrl = c->ctrl;
+    L.lamw = c->lamw;
+    L.nodes = c->nodes;
+    L.nx = c->cfg.nx;
+    L.ny = c->cfg.ny;
+    L.pitch = c->pitch;
+    L.plane = c->plane;
+    L.dx = c->dx;
+    L.dy = c->dy;
+    L.xmin = c->cfg.xmin;
+    L.ymin = c->cfg.ymin;
+    L.pol = pol;
+    L.K = c->cfg.params[0];
+    L.theta = c->cfg.params[1];
+    L.ug_mode = (int)c->cfg.params[2];
+    L.Q = c->spray_Q;
+    L.tol = c->cfg.params[4] > 0.0 ? c->cfg.params[4] : 1e-13;
+    e = launch_spray_source(L, c->src_grid, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spray source launch");
+  }
   return FV_OK;
 }
 
@@ -311,6 +345,27 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     return bail(e, "cudaMalloc(partials)");
   if ((e = cudaMalloc(&c->d_totals, sizeof(double) * 8)) != cudaSuccess) return bail(e, "cudaMalloc(totals)");
   if ((e = cudaMemset(c->ctrl, 0, sizeof(Ctrl))) != cudaSuccess) return bail(e, "cudaMemset");
+  if (cfg->system == FV_SPRAY) {
+    const int Q = cfg->params[3] > 0.0 ? (int)cfg->params[3] : 32;
+    std::vector<double> x(Q), w(Q), tab((size_t)Q * kSprayNodeStride);
+    fv_gauss_legendre(Q, x.data(), w.data());
+    for (int q = 0; q < Q; ++q) {
+      double *r = &tab[(size_t)q * kSprayNodeStride];
+      r[0] = x[q];
+      double xk = 1.0;
+      for (int k = 0; k < 7; ++k) {
+        r[1 + k] = w[q] * 2.0 * x[q] * xk;  // weight of S^(k/2) n(S) dS in x = sqrt(S)
+        xk *= x[q];
+      }
+      r[8] = 2.0 * w[q];                    // weight of S^(-1/2) n(S) dS
+    }
+    c->spray_Q = Q;
+    if ((e = cudaMalloc(&c->nodes, sizeof(double) * tab.size())) != cudaSuccess) return bail(e, "cudaMalloc(nodes)");
+    if ((e = cudaMemcpy(c->nodes, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "cudaMemcpy(nodes)");
+    if ((e = cudaMalloc(&c->lamw, sizeof(double) * 4 * c->plane)) != cudaSuccess) return bail(e, "cudaMalloc(lamw)");
+    c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, c->sms);
+  }
   int prec = cfg->precision == FV_F64 ? 0 : 1;
   int vi = default_variant(cfg->system, prec);
   if (cfg->tune >= 2) {
@@ -347,6 +402,8 @@ extern "C" void fv_destroy(fv_ctx *c) {
   if (c->staging) cudaFree(c->staging);
   if (c->partials) cudaFree(c->partials);
   if (c->d_totals) cudaFree(c->d_totals);
+  if (c->lamw) cudaFree(c->lamw);
+  if (c->nodes) cudaFree(c->nodes);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
@@ -373,8 +430,8 @@ static fv_status seed(fv_ctx *c, long long step, double t) {
   h.t = t;
   *c->h_ctrl = h;
   FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
-  const int cur = c->cfg.system == FV_EULER ? 0 : 0;
-  (void)cur;
+  if (c->lamw)  // all-ones bytes are NaNs: every cell starts its Newton solve cold
+    FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 4 * c->plane, c->stream));
   double p0 = c->cfg.params[0], p1 = c->cfg.params[1];
   if (c->cfg.system == FV_EULER) p1 = c->cfg.params[0] - 1.0;
   FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision == FV_F64 ? 0 : 1, c->buf[step & 1],
@@ -452,11 +509,63 @@ extern "C" fv_status fv_get_state(fv_ctx *c, void *dst, int dst_is_device, int d
   return FV_OK;
 }
 
+// Autotuner: time every compiled candidate of this (system, precision) on
+// one step from the current state and keep the fastest.  The control block
+// is restored before every trial launch and at the end, so the state, t and
+// n are untouched (a trial only writes the other ping-pong buffer).
+static fv_status autotune(fv_ctx *c) {
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  Ctrl saved = *c->h_ctrl;
+  const Variant &cur = all_variants()[c->variant];
+  auto cand = candidates(cur.system, cur.precision);
+  cudaEvent_t e0, e1;
+  FV_CUDA(c, cudaEventCreate(&e0));
+  FV_CUDA(c, cudaEventCreate(&e1));
+  int best = c->variant;
+  float best_ms = 1e30f;
+  for (int vi : cand) {
+    st = select_variant(c, vi);
+    if (st != FV_OK) break;
+    std::vector<float> ms;
+    for (int rep = 0; rep < 4 && st == FV_OK; ++rep) {
+      *c->h_ctrl = saved;
+      FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+      FV_CUDA(c, cudaEventRecord(e0, c->stream));
+      st = launch_step(c, c->stream);
+      FV_CUDA(c, cudaEventRecord(e1, c->stream));
+      FV_CUDA(c, cudaEventSynchronize(e1));
+      float t = 0;
+      FV_CUDA(c, cudaEventElapsedTime(&t, e0, e1));
+      if (rep > 0) ms.push_back(t);
+    }
+    if (st != FV_OK) break;
+    std::sort(ms.begin(), ms.end());
+    const float med = ms[ms.size() / 2];
+    if (med < best_ms) {
+      best_ms = med;
+      best = vi;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *c->h_ctrl = saved;
+  FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+  FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st != FV_OK) return st;
+  c->tuned = true;
+  return select_variant(c, best);
+}
+
 extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) {
   if (!c) return FV_ERR_INVALID_ARG;
   if (nsteps < 0) return fail(c, FV_ERR_INVALID_ARG, "nsteps < 0");
   if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
   if (!std::isfinite(t_end)) return fail(c, FV_ERR_INVALID_ARG, "t_end must be finite");
+  if (c->cfg.tune == 1 && !c->tuned && nsteps > 0) {
+    fv_status st = autotune(c);
+    if (st != FV_OK) return st;
+  }
   *c->h_scalar = t_end;
   FV_CUDA(c, cudaMemcpyAsync(&c->ctrl->t_end, c->h_scalar, sizeof(double), cudaMemcpyHostToDevice,
                              c->stream));
@@ -585,5 +694,13 @@ extern "C" fv_status fv_gauss_legendre(int Q, double *x, double *w) {
     x[Q - 1 - i] = 0.5 * (1.0 + t);
     w[Q - 1 - i] = 1.0 / ((1.0 - t * t) * d * d);
   }
+  return FV_OK;
+}
+
+extern "C" fv_status fv_kernel_candidate(int system, int precision, int index, const char **desc) {
+  if (!desc || (precision != FV_F64 && precision != FV_F32)) return FV_ERR_INVALID_ARG;
+  auto cand = candidates(system, precision == FV_F64 ? 0 : 1);
+  if (index < 0 || index >= (int)cand.size()) return FV_ERR_INVALID_ARG;
+  *desc = all_variants()[cand[index]].desc;
   return FV_OK;
 }

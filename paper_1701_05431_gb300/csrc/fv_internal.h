@@ -17,6 +17,7 @@ struct Variant {
   int V;           // cells per lane along x
   int TY;          // rows per warp task
   int NW;          // warps per block
+  int MINB;        // blocks per SM the register budget is cut for
   const void *kernel;
   const char *desc;
 };
@@ -43,6 +44,21 @@ cudaError_t launch_totals(int prec, int nvar, const void *state, int nx, int ny,
 int totals_blocks(int ny);
 
 // Spray source step (fv_spray.cu).
-struct SprayArgs;
+struct SourceLaunch {
+  int prec;
+  void *buf0, *buf1;
+  Ctrl *ctrl;
+  double *lamw;
+  const double *nodes;
+  int nx, ny;
+  long long pitch, plane;
+  double dx, dy, xmin, ymin;
+  DtPolicy pol;
+  double K, theta, tol;
+  int ug_mode, Q;
+};
+int spray_source_grid(int prec, int sms);
+cudaError_t launch_spray_source(const SourceLaunch &L, int grid, cudaStream_t s);
+constexpr int kSprayNodeStride = 9;
 
 }  // namespace fv

@@ -1,0 +1,300 @@
+// fv_spray.cu -- split source step of the evaporating-spray moment system
+// (arXiv:1701.05431, Sec. 2.2.2 Eq. (SourceTerm), Sec. 6.1 Eq. (Essadki),
+// Sec. 6.2): W^{n+1} = W* + dt S(W*) per cell, where the evaporation terms
+// need n(S = 0) and m_{-1/2} of the maximum-entropy size distribution
+// n(S) = exp(-(lam0 + lam1 S^1/2 + lam2 S + lam3 S^3/2)) that matches the
+// moments m0, m1/2, m1, m3/2.
+//
+// One thread per cell.  The multipliers are found by damped Newton on the
+// convex dual, in FP64 in every storage precision (an FP32 Hessian of these
+// Hankel-type moment matrices loses too many digits); the moments of a trial
+// density are Gauss-Legendre sums in x = sqrt(S) whose nodes and
+// pre-multiplied weights sit in shared memory.  The multipliers of each cell
+// are kept between steps (warm start): the moments move by O(dt) per step, so
+// Newton usually needs three or four moment evaluations instead of eight.
+// After the update the kernel reduces lmax(W^{n+1}) and closes the step.
+#include <cuda_runtime.h>
+
+#include "fv_device.cuh"
+#include "fv_internal.h"
+#include "fv_step.cuh"
+
+namespace fv {
+
+constexpr int kSrcThreads = 128;
+constexpr int kSrcWarps = kSrcThreads / 32;
+constexpr int kMaxQ = 64;
+constexpr int kNodeStride = 9;  // x, w 2x x^k (k = 0..6), 2w
+
+template <class R> struct SourceArgs {
+  R *buf0;
+  R *buf1;
+  Ctrl *ctrl;
+  double *lamw;          // 4 planes of ny x pitch warm-start multipliers
+  const double *nodes;   // Q x kNodeStride
+  int nx, ny;
+  long long pitch, plane;
+  double dx, dy, xmin, ymin;
+  DtPolicy pol;
+  double K, theta, tol;
+  int ug_mode, Q;
+};
+
+// Moments M_k = sum_q w_q 2 x_q x_q^k n(x_q^2), k = 0..6, and
+// M_{-1} = sum_q 2 w_q n(x_q^2) (= m_{-1/2}) of the trial density.
+static __device__ __forceinline__ void me_moments(const double *nd, int Q, const double (&lam)[4],
+                                                  double (&M)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) M[k] = 0.0;
+  for (int q = 0; q < Q; ++q) {
+    const double *r = nd + q * kNodeStride;
+    const double x = r[0];
+    const double poly = fma(fma(fma(lam[3], x, lam[2]), x, lam[1]), x, lam[0]);
+    const double e = exp(-poly);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) M[k] = fma(r[1 + k], e, M[k]);
+    M[7] = fma(r[8], e, M[7]);
+  }
+}
+
+// Cholesky solve of the 4 x 4 SPD system H d = r; false if H is not SPD.
+static __device__ __forceinline__ bool spd_solve4(const double (&M)[8], const double (&r)[4],
+                                                  double (&d)[4]) {
+  double L[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      double s = M[i + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        L[i][i] = sqrt(s);
+      } else {
+        L[i][j] = s / L[j][j];
+      }
+    }
+  }
+  double y[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    double s = r[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+    y[i] = s / L[i][i];
+  }
+#pragma unroll
+  for (int i = 3; i >= 0; --i) {
+    double s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 4; ++k) s -= L[k][i] * d[k];
+    d[i] = s / L[i][i];
+  }
+  return true;
+}
+
+// Interior of the moment space of measures on [0,1] (positive Hankel
+// determinants of the measure and of its products with x and 1 - x).
+static __device__ __forceinline__ bool realizable(const double (&c)[4]) {
+  return c[0] > 0.0 && c[1] > 0.0 && c[0] - c[1] > 0.0 && c[0] * c[2] - c[1] * c[1] > 0.0 &&
+         c[1] - c[2] > 0.0 && c[1] * c[3] - c[2] * c[2] > 0.0 &&
+         (c[0] - c[1]) * (c[2] - c[3]) - (c[1] - c[2]) * (c[1] - c[2]) > 0.0;
+}
+
+// Maximum-entropy reconstruction: returns false when Newton fails.
+static __device__ bool maxent(const double *nd, int Q, double tol, const double (&m)[4], double (&lam)[4],
+                              double &n0, double &mmh) {
+  double M[8];
+  bool ok = false;
+  for (int it = 0; it < 100; ++it) {
+    me_moments(nd, Q, lam, M);
+    double r[4], worst = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      r[k] = M[k] - m[k];
+      worst = fmax(worst, fabs(r[k]) / m[k]);
+    }
+    if (worst <= tol) {
+      ok = true;
+      break;
+    }
+    if (!(worst == worst)) return false;
+    double d[4];
+    if (!spd_solve4(M, r, d)) return false;
+    if (worst >= 1e-3) {
+      // far from the solution: halve the step until the dual
+      // Phi = int n dS + sum lam_k m_k decreases (Armijo)
+      const double phi0 = M[0] + lam[0] * m[0] + lam[1] * m[1] + lam[2] * m[2] + lam[3] * m[3];
+      const double slope = -(r[0] * d[0] + r[1] * d[1] + r[2] * d[2] + r[3] * d[3]);
+      double alpha = 1.0, trial[4];
+      for (int ls = 0; ls < 60; ++ls) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) trial[k] = lam[k] + alpha * d[k];
+        double Mt[8];
+        me_moments(nd, Q, trial, Mt);
+        const double phi = Mt[0] + trial[0] * m[0] + trial[1] * m[1] + trial[2] * m[2] + trial[3] * m[3];
+        if (phi <= phi0 + 1e-4 * alpha * slope + 4e-16 * fabs(phi0)) break;
+        alpha *= 0.5;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) lam[k] = trial[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) lam[k] += d[k];
+    }
+  }
+  if (!ok) {
+    // accept a result that stalled at round-off level
+    me_moments(nd, Q, lam, M);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (!(fabs(M[k] - m[k]) <= 1e-10 * m[k])) return false;
+  }
+  n0 = exp(-lam[0]);
+  mmh = M[7];
+  return true;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kSrcThreads)
+fv_spray_source_kernel(const SourceArgs<R> a) {
+  __shared__ double s_lam[kSrcWarps];
+  __shared__ int s_bad[kSrcWarps];
+  __shared__ StepStart s_st;
+  __shared__ double s_nodes[kMaxQ * kNodeStride];
+  for (int k = threadIdx.x; k < a.Q * kNodeStride; k += blockDim.x) s_nodes[k] = a.nodes[k];
+  if (threadIdx.x == 0) s_st = read_step_start(a.pol, a.ctrl);
+  __syncthreads();
+  const StepStart st = s_st;
+  double lmax = 0.0;
+  bool bad = false;
+  if (st.run) {
+    R *__restrict__ W = ((st.step + 1) & 1) ? a.buf1 : a.buf0;  // the transport output
+    const double dt = st.dt;
+    const long long ncell = (long long)a.nx * a.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
+         k += (long long)gridDim.x * blockDim.x) {
+      const int j = (int)(k / a.nx), i = (int)(k % a.nx);
+      const long long o = (long long)j * a.pitch + i;
+      double w[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) w[v] = (double)W[v * a.plane + o];
+      const double m[4] = {w[0], w[1], w[2], w[3]};
+      bool cell_bad = !realizable(m);
+      double lam[4];
+      const double warm0 = a.lamw[o];
+      if (warm0 == warm0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lam[q] = a.lamw[q * a.plane + o];
+      } else {
+        lam[0] = -log(m[0]);
+        lam[1] = lam[2] = lam[3] = 0.0;
+      }
+      double n0 = 0.0, mmh = 0.0;
+      if (!cell_bad) cell_bad = !maxent(s_nodes, a.Q, a.tol, m, lam, n0, mmh);
+      if (!cell_bad) {
+        const double K = a.K;
+        const double u = w[4] / w[2], v = w[5] / w[2];
+        double S[6];
+        S[0] = -K * n0;
+        S[1] = -K / 2.0 * mmh;
+        S[2] = -K * m[0];
+        S[3] = -3.0 * K / 2.0 * m[1];
+        S[4] = -K * m[0] * u;
+        S[5] = -K * m[0] * v;
+        if (a.theta > 0.0) {
+          double ug = 0.0, vg = 0.0;
+          if (a.ug_mode == 1) {
+            const double x = a.xmin + (i + 0.5) * a.dx, y = a.ymin + (j + 0.5) * a.dy;
+            ug = sinpi(2.0 * x) * cospi(2.0 * y);
+            vg = -cospi(2.0 * x) * sinpi(2.0 * y);
+          }
+          S[4] += m[0] * (ug - u) / a.theta;
+          S[5] += m[0] * (vg - v) / a.theta;
+        }
+        R wn[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) wn[q] = (R)(w[q] + dt * S[q]);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) W[q * a.plane + o] = wn[q];
+        const double c[4] = {(double)wn[0], (double)wn[1], (double)wn[2], (double)wn[3]};
+        cell_bad = !realizable(c);
+        SysParams<R> P{(R)0, (R)0};
+        bool b;
+        const R l = Spray::lambda<R>(wn, P, b);
+        cell_bad |= b;
+        lmax = fmax(lmax, (double)l);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a.lamw[q * a.plane + o] = lam[q];
+      } else {
+        a.lamw[o] = __longlong_as_double(0x7ff8000000000000LL);
+      }
+      bad |= cell_bad;
+    }
+  }
+  finish_step<kSrcWarps>(a.ctrl, st, lmax, bad, s_lam, s_bad);
+}
+
+template <class R>
+static SourceArgs<R> make_source_args(const SourceLaunch &L) {
+  SourceArgs<R> a;
+  a.buf0 = (R *)L.buf0;
+  a.buf1 = (R *)L.buf1;
+  a.ctrl = L.ctrl;
+  a.lamw = L.lamw;
+  a.nodes = L.nodes;
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.pitch = L.pitch;
+  a.plane = L.plane;
+  a.dx = L.dx;
+  a.dy = L.dy;
+  a.xmin = L.xmin;
+  a.ymin = L.ymin;
+  a.pol = L.pol;
+  a.K = L.K;
+  a.theta = L.theta;
+  a.tol = L.tol;
+  a.ug_mode = L.ug_mode;
+  a.Q = L.Q;
+  return a;
+}
+
+int spray_source_grid(int prec, int sms) {
+  int nb = 0;
+  const void *k = prec == 0 ? (const void *)&fv_spray_source_kernel<double>
+                            : (const void *)&fv_spray_source_kernel<float>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kSrcThreads, 0) != cudaSuccess || nb < 1)
+    nb = 1;
+  return nb * sms;
+}
+
+cudaError_t launch_spray_source(const SourceLaunch &L, int grid, cudaStream_t s) {
+  long long need = ((long long)L.nx * L.ny + kSrcThreads - 1) / kSrcThreads;
+  if (need < grid) grid = (int)need;
+  if (grid < 1) grid = 1;
+  if (L.prec == 0) {
+    SourceArgs<double> a = make_source_args<double>(L);
+    fv_spray_source_kernel<double><<<grid, kSrcThreads, 0, s>>>(a);
+  } else {
+    SourceArgs<float> a = make_source_args<float>(L);
+    fv_spray_source_kernel<float><<<grid, kSrcThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Transport step kernels of the spray system (the source kernel closes the
+// step, so they run with finalize = 0).
+#define FV_VARIANT(R, PREC, V, TY, NW, MB, DESC)                                                  \
+  out.push_back(Variant{kSpray, PREC, V, TY, NW, MB,                                               \
+                        reinterpret_cast<const void *>(&fv_step_kernel<Spray, R, V, TY, NW, false, MB>), \
+                        DESC})
+
+void register_step_spray(std::vector<Variant> &out) {
+  FV_VARIANT(double, 0, 1, 32, 4, 1, "spray f64 v1 ty32 w4");
+  FV_VARIANT(float, 1, 1, 32, 4, 1, "spray f32 v1 ty32 w4");
+  FV_VARIANT(float, 1, 2, 32, 4, 1, "spray f32 v2 ty32 w4");
+}
+
+}  // namespace fv

@@ -38,7 +38,6 @@ template <class R> struct StepArgs {
   SysParams<R> sp;
   int bc[4];
   R bc_state[4][8];
-  int finalize;      // 1: this launch reduces lmax and closes the step
 };
 
 template <class R, int V> struct VecIO;
@@ -78,54 +77,82 @@ template <> struct VecIO<double, 2> {
   }
 };
 
-// Load V cells of row j starting at column X into W[c][v], applying the
-// boundary conditions for the ghost row/column just outside the domain.
-// Columns further out (only reached by the idle halo lane of a ragged strip)
-// are clamped to a real cell; their values are never used.
-template <int NV, int V, class R>
-static __device__ __forceinline__ void load_row(const StepArgs<R> &a, const R *__restrict__ src,
-                                                int j, int X, R (&W)[V][NV]) {
-  int side = -1, sj = j;
-  if (j < 0) {
-    side = kS;
-    sj = a.bc[kS] == kPeriodic ? a.ny - 1 : 0;
-  } else if (j >= a.ny) {
-    side = kN;
-    sj = a.bc[kN] == kPeriodic ? 0 : a.ny - 1;
+// Where a lane's V cells come from.  Interior strips (every lane's cells
+// inside [0, nx)) read V-wide vectors at column X; strips touching the east or
+// west boundary map each cell once per task: a real column, the ghost column
+// of the boundary condition, or (only for the idle halo lane of a ragged
+// strip) a clamped column whose values are never used.
+template <int V> struct LaneCols {
+  int col[V];
+  int dir[V];  // Dirichlet side of a ghost cell, -1 otherwise
+};
+
+template <int V, class R>
+static __device__ __forceinline__ LaneCols<V> lane_cols(const StepArgs<R> &a, int X) {
+  LaneCols<V> L;
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    const int col = X + c;
+    int sc = col, cs = -1;
+    if (col < 0) {
+      if (col == -1) cs = kW;
+      sc = (col == -1 && a.bc[kW] == kPeriodic) ? a.nx - 1 : 0;
+    } else if (col >= a.nx) {
+      if (col == a.nx) cs = kE;
+      sc = (col == a.nx && a.bc[kE] == kPeriodic) ? 0 : a.nx - 1;
+    }
+    L.col[c] = sc;
+    L.dir[c] = (cs >= 0 && a.bc[cs] == kDirichlet) ? cs : -1;
   }
-  if (side >= 0 && a.bc[side] == kDirichlet) {
+  return L;
+}
+
+// Source row of row j (ghost rows -1 and ny from the boundary condition);
+// returns the Dirichlet side when the ghost row is a prescribed state.
+template <class R>
+static __device__ __forceinline__ int row_src(const StepArgs<R> &a, int j, int &dir) {
+  dir = -1;
+  if (j < 0) {
+    if (a.bc[kS] == kDirichlet) dir = kS;
+    return a.bc[kS] == kPeriodic ? a.ny - 1 : 0;
+  }
+  if (j >= a.ny) {
+    if (a.bc[kN] == kDirichlet) dir = kN;
+    return a.bc[kN] == kPeriodic ? 0 : a.ny - 1;
+  }
+  return j;
+}
+
+template <int NV, int V, bool XIN, class R>
+static __device__ __forceinline__ void load_row(const StepArgs<R> &a, const R *__restrict__ base,
+                                                const LaneCols<V> &L, int j, R (&W)[V][NV]) {
+  int dir;
+  const int sj = row_src(a, j, dir);
+  if (dir >= 0) {
 #pragma unroll
     for (int c = 0; c < V; ++c)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[side][v];
+      for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[dir][v];
     return;
   }
-  const R *row = src + (long long)sj * a.pitch;
-  if (X >= 0 && X + V <= a.nx) {
+  const R *row = base + (long long)sj * a.pitch;
+  if (XIN) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       R t[V];
-      VecIO<R, V>::ld(row + v * a.plane + X, t);
+      VecIO<R, V>::ld(row + v * a.plane, t);
 #pragma unroll
       for (int c = 0; c < V; ++c) W[c][v] = t[c];
     }
   } else {
 #pragma unroll
     for (int c = 0; c < V; ++c) {
-      int col = X + c, sc = col, cs = -1;
-      if (col < 0) {
-        if (col == -1) { cs = kW; sc = a.bc[kW] == kPeriodic ? a.nx - 1 : 0; }
-        else sc = 0;
-      } else if (col >= a.nx) {
-        if (col == a.nx) { cs = kE; sc = a.bc[kE] == kPeriodic ? 0 : a.nx - 1; }
-        else sc = a.nx - 1;
-      }
-      if (cs >= 0 && a.bc[cs] == kDirichlet) {
+      if (L.dir[c] >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[cs][v];
+        for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[L.dir[c]][v];
       } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) W[c][v] = __ldg(row + v * a.plane + sc);
+        for (int v = 0; v < NV; ++v) W[c][v] = __ldg(row + v * a.plane + L.col[c]);
       }
     }
   }
@@ -170,45 +197,141 @@ static __device__ __forceinline__ void row_x(const SysParams<R> &P, const R (&W)
   }
 }
 
-template <class Sys, class R, int V, int TY, int NW>
-__global__ void __launch_bounds__(NW * 32)
-fv_step_kernel(const StepArgs<R> a) {
+// Registers of one row of the march.
+template <class R, int V, int NV> struct RowState {
+  R W[V][NV];
+  R Fy[V][NV];
+  R sy[V];
+  R dX[V][NV];
+};
+
+// One row of the march: `nxt` receives row j+1 (already prefetched in P),
+// P is refilled with row j+2, the y-face between rows j and j+1 is evaluated
+// once, row j is updated and stored (by the writer lanes), and the new
+// state's wave speed enters the running maximum.
+template <class Sys, class R, int V, bool XIN, bool FIN>
+static __device__ __forceinline__ void march_row(const StepArgs<R> &a, const R *__restrict__ src,
+                                                 R *__restrict__ dst_lane, const LaneCols<V> &L,
+                                                 int X, int j, int y1, bool writer, R lx, R ly,
+                                                 RowState<R, V, Sys::NV> &cur,
+                                                 RowState<R, V, Sys::NV> &nxt,
+                                                 R (&P)[V][Sys::NV], R (&Fs)[V][Sys::NV],
+                                                 R &lam_loc, bool &bad) {
   constexpr int NV = Sys::NV;
   using O = Ops<R>;
+#pragma unroll
+  for (int c = 0; c < V; ++c)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) nxt.W[c][v] = P[c][v];
+  if (j + 2 <= y1) load_row<NV, V, XIN>(a, src, L, j + 2, P);
+  row_x<Sys, V>(a.sp, nxt.W, nxt.Fy, nxt.sy, nxt.dX);
+  R Wn[V][NV];
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    const R hs = O::mul((R)0.5, O::max(cur.sy[c], nxt.sy[c]));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R Fn = lf_face(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], hs);
+      Wn[c][v] = fv_update(cur.W[c][v], cur.dX[c][v], O::sub(Fn, Fs[c][v]), lx, ly);
+      Fs[c][v] = Fn;
+    }
+  }
+  if (writer) {
+    R *row = dst_lane + (long long)j * a.pitch;
+    if (XIN || X + V <= a.nx) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        R t[V];
+#pragma unroll
+        for (int c = 0; c < V; ++c) t[c] = Wn[c][v];
+        VecIO<R, V>::st(row + v * a.plane, t);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < V; ++c)
+        if (X + c < a.nx) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) __stcs(row + v * a.plane + c, Wn[c][v]);
+        }
+    }
+    if (FIN) {
+#pragma unroll
+      for (int c = 0; c < V; ++c) {
+        if (XIN || X + c < a.nx) {
+          bool b;
+          const R l = Sys::lambda(Wn[c], a.sp, b);
+          lam_loc = O::max(lam_loc, l);
+          bad |= b;
+        }
+      }
+    }
+  }
+}
+
+// March one warp task: rows [y0, y1) of the strip whose lane l holds the V
+// cells starting at column X.
+template <class Sys, class R, int V, bool XIN, bool FIN>
+static __device__ __forceinline__ void march(const StepArgs<R> &a, const R *__restrict__ src,
+                                             R *__restrict__ dst, int X, int y0, int y1, bool writer,
+                                             R lx, R ly, R &lam_loc, bool &bad) {
+  constexpr int NV = Sys::NV;
+  using O = Ops<R>;
+  LaneCols<V> L;
+  if (!XIN) L = lane_cols<V>(a, X);
+  const R *base = XIN ? src + X : src;
+  R *dst_lane = dst + X;
+  RowState<R, V, NV> A, B;
+  R P[V][NV], Fs[V][NV];
+  // row below the strip: only its y-fluxes are needed
+  load_row<NV, V, XIN>(a, base, L, y0 - 1, A.W);
+  load_row<NV, V, XIN>(a, base, L, y0, B.W);
+  if (y0 + 1 <= y1) load_row<NV, V, XIN>(a, base, L, y0 + 1, P);
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    R Fx_[NV], sx_;
+    Sys::fluxes(A.W[c], a.sp, Fx_, sx_, A.Fy[c], A.sy[c]);
+  }
+  row_x<Sys, V>(a.sp, B.W, B.Fy, B.sy, B.dX);
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    const R hs = O::mul((R)0.5, O::max(A.sy[c], B.sy[c]));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(A.W[c][v], A.Fy[c][v], B.W[c][v], B.Fy[c][v], hs);
+  }
+  // the two row states swap roles every row (unrolled by two: no copies)
+  int j = y0;
+  while (true) {
+    if (j >= y1) break;
+    march_row<Sys, R, V, XIN, FIN>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, B, A, P, Fs, lam_loc, bad);
+    ++j;
+    if (j >= y1) break;
+    march_row<Sys, R, V, XIN, FIN>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, A, B, P, Fs, lam_loc, bad);
+    ++j;
+  }
+}
+
+// FIN: this launch also reduces lmax(W^{n+1}) and closes the step (every
+// system but spray, whose source kernel closes the step instead).
+template <class Sys, class R, int V, int TY, int NW, bool FIN = true, int MINB = 1>
+__global__ void __launch_bounds__(NW * 32, MINB)
+fv_step_kernel(const StepArgs<R> a) {
   __shared__ double s_lam[NW];
   __shared__ int s_bad[NW];
-  __shared__ double s_dt;
-  __shared__ int s_run;
-  __shared__ unsigned s_err;
-  __shared__ long long s_step;
-
-  if (threadIdx.x == 0) {
-    Ctrl c;
-    c.step = __ldcg(&a.ctrl->step);
-    c.t = __ldcg(&a.ctrl->t);
-    c.t_end = __ldcg(&a.ctrl->t_end);
-    c.err_committed = __ldcg(&a.ctrl->err_committed);
-    const double lam = lam_value(__ldcg(&a.ctrl->lam[c.step % 3]));
-    double dt = 0.0;
-    unsigned err = 0u;
-    s_run = choose_dt(a.pol, c, lam, &dt, &err) ? 1 : 0;
-    s_dt = dt;
-    s_err = err;
-    s_step = c.step;
-  }
+  __shared__ StepStart s_st;
+  if (threadIdx.x == 0) s_st = read_step_start(a.pol, a.ctrl);
   __syncthreads();
-  const int run = s_run;
-  const long long n = s_step;
+  const StepStart st = s_st;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   R lam_loc = (R)0;
   bool bad = false;
 
-  if (run) {
+  if (st.run) {
+    const long long n = st.step;
     const R *__restrict__ src = (n & 1) ? a.buf1 : a.buf0;
     R *__restrict__ dst = (n & 1) ? a.buf0 : a.buf1;
-    const R lx = (R)(s_dt / a.dx);
-    const R ly = (R)(s_dt / a.dy);
+    const R lx = (R)(st.dt / a.dx);
+    const R ly = (R)(st.dt / a.dy);
     const bool writer = lane >= 1 && lane <= 30;
     const int gw = blockIdx.x * NW + warp;
     const int GW = gridDim.x * NW;
@@ -218,129 +341,15 @@ fv_step_kernel(const StepArgs<R> a) {
       const int X = sx_ * (30 * V) + (lane - 1) * V;
       const int y0 = cy * TY;
       const int y1 = min(y0 + TY, a.ny);
-
-      R Wa[V][NV], Fya[V][NV], sya[V], dXa[V][NV], Fs[V][NV];
-      R Wb[V][NV], Fyb[V][NV], syb[V], dXb[V][NV];
-      R Wp[V][NV];
-      // row below the strip: only its y-fluxes are needed
-      load_row<NV, V>(a, src, y0 - 1, X, Wa);
-      load_row<NV, V>(a, src, y0, X, Wb);
-      if (y0 + 1 <= y1) load_row<NV, V>(a, src, y0 + 1, X, Wp);
-#pragma unroll
-      for (int c = 0; c < V; ++c) {
-        R Fx_[NV], sx_unused;
-        Sys::fluxes(Wa[c], a.sp, Fx_, sx_unused, Fya[c], sya[c]);
-      }
-      row_x<Sys, V>(a.sp, Wb, Fyb, syb, dXb);
-#pragma unroll
-      for (int c = 0; c < V; ++c) {
-        const R hs = O::mul((R)0.5, O::max(sya[c], syb[c]));
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          Fs[c][v] = lf_face(Wa[c][v], Fya[c][v], Wb[c][v], Fyb[c][v], hs);
-          Wa[c][v] = Wb[c][v];
-          Fya[c][v] = Fyb[c][v];
-          dXa[c][v] = dXb[c][v];
-        }
-        sya[c] = syb[c];
-      }
-
-      for (int j = y0; j < y1; ++j) {
-#pragma unroll
-        for (int c = 0; c < V; ++c)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) Wb[c][v] = Wp[c][v];
-        if (j + 2 <= y1) load_row<NV, V>(a, src, j + 2, X, Wp);
-        row_x<Sys, V>(a.sp, Wb, Fyb, syb, dXb);
-        R Wn[V][NV];
-#pragma unroll
-        for (int c = 0; c < V; ++c) {
-          const R hs = O::mul((R)0.5, O::max(sya[c], syb[c]));
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const R Fn = lf_face(Wa[c][v], Fya[c][v], Wb[c][v], Fyb[c][v], hs);
-            Wn[c][v] = fv_update(Wa[c][v], dXa[c][v], O::sub(Fn, Fs[c][v]), lx, ly);
-            Fs[c][v] = Fn;
-            Wa[c][v] = Wb[c][v];
-            Fya[c][v] = Fyb[c][v];
-            dXa[c][v] = dXb[c][v];
-          }
-          sya[c] = syb[c];
-        }
-        if (writer) {
-          R *row = dst + (long long)j * a.pitch;
-          if (X + V <= a.nx) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-              R t[V];
-#pragma unroll
-              for (int c = 0; c < V; ++c) t[c] = Wn[c][v];
-              VecIO<R, V>::st(row + v * a.plane + X, t);
-            }
-          } else {
-#pragma unroll
-            for (int c = 0; c < V; ++c)
-              if (X + c < a.nx) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) __stcs(row + v * a.plane + X + c, Wn[c][v]);
-              }
-          }
-          if (a.finalize) {
-#pragma unroll
-            for (int c = 0; c < V; ++c) {
-              if (X + c < a.nx) {
-                bool b;
-                const R l = Sys::lambda(Wn[c], a.sp, b);
-                lam_loc = O::max(lam_loc, l);
-                bad |= b;
-              }
-            }
-          }
-        }
-      }
+      // warp-uniform: does every lane of the strip read real columns only?
+      const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
+      if (xin) march<Sys, R, V, true, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else march<Sys, R, V, false, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }
   }
 
-  if (!a.finalize) return;
-  // block reduction of lmax(W^{n+1}) and of the admissibility flag
-  double l = (double)lam_loc;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
-  const int anybad = __any_sync(0xffffffffu, bad);
-  if (lane == 0) {
-    s_lam[warp] = l;
-    s_bad[warp] = anybad;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double bl = 0.0;
-    int bb = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      bl = fmax(bl, s_lam[w]);
-      bb |= s_bad[w];
-    }
-    Ctrl *ctrl = a.ctrl;
-    if (run) {
-      if (bl > 0.0 || bb) atomicMax(&ctrl->lam[(n + 1) % 3], lam_bits(bb ? __longlong_as_double(0x7ff8000000000000LL) : bl));
-      if (bb) atomicOr(&ctrl->err_pending, kErrNonphysical);
-    }
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
-    if (prev == gridDim.x - 1) {
-      __threadfence();
-      ctrl->blocks_done = 0u;
-      unsigned e = atomicExch(&ctrl->err_pending, 0u) | s_err;
-      if (run) {
-        ctrl->t = ctrl->t + s_dt;
-        ctrl->dt_last = s_dt;
-        ctrl->step = n + 1;
-        ctrl->lam[(n + 2) % 3] = 0ull;
-      }
-      if (e) ctrl->err_committed |= e;
-      __threadfence();
-    }
-  }
+  if (!FIN) return;
+  finish_step<NW>(a.ctrl, st, (double)lam_loc, bad, s_lam, s_bad);
 }
 
 }  // namespace fv

@@ -57,7 +57,7 @@ _lib = None
 
 EXPORTS = ("fv_status_string", "fv_last_error", "fv_init", "fv_destroy", "fv_set_state", "fv_step",
            "fv_run", "fv_get_state", "fv_totals", "fv_time", "fv_set_time", "fv_lambda_max",
-           "fv_kernel_info", "fv_gauss_legendre")
+           "fv_kernel_info", "fv_kernel_candidate", "fv_gauss_legendre")
 
 
 def library_path() -> str:
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.fv_lambda_max.argtypes = [vp, dp]
     L.fv_kernel_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_char_p)]
     L.fv_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
+    L.fv_kernel_candidate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p)]
     for name in EXPORTS:
         if name not in ("fv_status_string", "fv_last_error", "fv_destroy"):
             getattr(L, name).restype = ctypes.c_int
@@ -266,6 +267,16 @@ class Solver:
         d = ctypes.c_char_p()
         _check(self.lib.fv_kernel_info(self.ctx, ctypes.byref(v), ctypes.byref(d)), self.ctx, self.lib)
         return v.value, d.value.decode()
+
+
+def kernel_candidates(system: str, precision: str):
+    """Descriptions of the compiled step-kernel candidates, in index order."""
+    L = load()
+    out = []
+    d = ctypes.c_char_p()
+    while L.fv_kernel_candidate(SYSTEMS[system], PRECISIONS[precision], len(out), ctypes.byref(d)) == FV_OK:
+        out.append(d.value.decode())
+    return out
 
 
 def gauss_legendre(Q: int):

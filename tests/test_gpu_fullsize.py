@@ -1,0 +1,95 @@
+"""Full-size parity in the benchmarked launch configuration, against sampled
+FP64-oracle outputs written by tests/golden/make_oracle_samples.py (the
+oracle needs minutes for these sizes, so it is not rerun here).
+
+  C2: Euler 2048^2, four-quadrant Riemann data, 8 x 8 subdomains,
+      transmissive, CFL 0.4, 500 steps, FP64.
+  C3: Euler 8192^2, smooth periodic data, CFL 0.4, 100 steps, FP64 and FP32.
+
+FP64 <= 1e-12 relative L-infinity per variable over the samples; FP32
+<= 1e-5 relative L1 over the samples (smooth data).
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests.helpers import transpose_state
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def fv():
+    from paper_1701_05431_gb300 import fvlib
+    return fvlib
+
+
+def golden(name):
+    return np.load(os.path.join(GOLDEN, f"{name}_oracle_samples.npz"))
+
+
+def run_full(d, prim, steps, precision, tune=0):
+    f = fv()
+    with f.Solver(d, precision, stream=torch.cuda.current_stream().cuda_stream, tune=tune) as s:
+        s.set_state(torch.from_numpy(prim).cuda(), primitive=True)
+        t = s.run(steps)
+        return s.state(), t, s
+
+
+def sampled(W, idx):
+    return W.reshape(W.shape[0], -1)[:, idx]
+
+
+def test_c2_four_quadrant_2048_fp64():
+    g = golden("c2")
+    prim, d = wl.four_quadrant(2048, npart=8)
+    W, t, _ = run_full(d, prim, int(g["steps"]), "f64")
+    got = sampled(W, g["flat_index"])
+    ref = g["W"]
+    err = np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert err.max() <= 1e-12, err
+    assert abs(t - float(g["t"])) <= 1e-13 * float(g["t"])
+    # the four-quadrant problem is symmetric under x <-> y, u <-> v
+    assert np.array_equal(transpose_state(W, "euler"), W)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_c3_smooth_8192(precision):
+    g = golden("c3")
+    prim, d = wl.smooth_periodic(8192)
+    W, t, _ = run_full(d, prim, int(g["steps"]), precision)
+    got = sampled(W, g["flat_index"])
+    ref = g["W"]
+    if precision == "f64":
+        err = np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)
+        assert err.max() <= 1e-12, err
+        assert abs(t - float(g["t"])) <= 1e-13 * float(g["t"])
+    else:
+        l1 = np.abs(got - ref).sum(axis=1) / np.abs(ref).sum(axis=1)
+        assert l1.max() <= 1e-5, l1
+        assert abs(t - float(g["t"])) <= 1e-5 * float(g["t"])
+
+
+def test_c3_conservation_fp64_full():
+    prim, d = wl.smooth_periodic(8192)
+    f = fv()
+    with f.Solver(d, "f64") as s:
+        s.set_state(torch.from_numpy(prim).cuda(), primitive=True)
+        t0 = s.totals()
+        W = s.state()
+        s.run(100)
+        t1 = s.totals()
+    mass = np.abs(W).sum(axis=(1, 2)) / 8192 ** 2
+    assert np.all(np.abs(t1 - t0) / mass <= 1e-13), np.abs(t1 - t0) / mass
