@@ -175,6 +175,58 @@ fv_status fv_kernel_candidate(int system, int precision, int index, const char *
  * library on the host.  1 <= Q <= 128. */
 fv_status fv_gauss_legendre(int Q, double *x, double *w);
 
+/* ------------------------------------------------------------------------
+ * Batched instances.  Many independent problems of the same system and
+ * precision (advection or Euler; sizes, boundary conditions, parameters and
+ * CFL may differ) advance together: one persistent kernel per fv_batch_run,
+ * captured in a CUDA graph, takes warp tasks (instance, strip, rows) of all
+ * instances and steps in a fixed increasing order; every instance keeps its
+ * own dt_n = cfl min(dx,dy)/lmax(W^n) (Eq. (CFL_cond)) and t.  Each
+ * instance's step is the same fused step as fv_run, with identical
+ * arithmetic: an instance run in a batch gives the same bits as run alone.
+ * Waits between the steps of an instance are bounded (2 s by default); a
+ * wait that runs out ends the launch with FV_ERR_TIMEOUT.
+ * ------------------------------------------------------------------------ */
+typedef struct fv_batch fv_batch;
+
+/* Validate n >= 1 configurations (same system, precision, stream and tune;
+ * spray is not batched) and allocate every instance's two state buffers in
+ * one device arena.  tune >= 2 forces batched kernel candidate tune - 2. */
+fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out);
+
+/* Load instance k's state at t = 0, step 0 (same conventions as
+ * fv_set_state).  Synchronises the stream. */
+fv_status fv_batch_set_state(fv_batch *b, int k, const void *src, int src_is_device, int src_dtype,
+                             int layout);
+
+/* Advance every instance by nsteps steps in one persistent launch.  Returns
+ * the first error raised by any instance (FV_ERR_CFL, FV_ERR_NONPHYSICAL,
+ * FV_ERR_INVALID_ARG for lmax = 0) or FV_ERR_TIMEOUT; an instance that
+ * failed keeps its last good state and stops advancing.  Synchronises. */
+fv_status fv_batch_run(fv_batch *b, int nsteps);
+
+/* Copy instance k's conserved state out (same conventions as
+ * fv_get_state).  Synchronises the stream. */
+fv_status fv_batch_get_state(fv_batch *b, int k, void *dst, int dst_is_device, int dst_dtype);
+
+/* Time and step count of instance k. */
+fv_status fv_batch_time(fv_batch *b, int k, double *t, long long *step);
+
+/* Kernel candidate in use (see fv_kernel_info). */
+fv_status fv_batch_kernel_info(fv_batch *b, int *variant, const char **desc);
+
+/* Limit of every wait between steps (seconds, 0 < s <= 60) and, for tests
+ * of the timeout path, an instance whose steps are never released
+ * (-1: none); that instance's next step then waits until the limit and the
+ * run returns FV_ERR_TIMEOUT without touching the GPU's health. */
+fv_status fv_batch_set_wait_limit(fv_batch *b, double seconds, int never_release_instance);
+
+/* Detail of the last failure on this batch ("" if none). */
+const char *fv_batch_last_error(const fv_batch *b);
+
+/* Release every buffer of the batch.  NULL is accepted. */
+void fv_batch_destroy(fv_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

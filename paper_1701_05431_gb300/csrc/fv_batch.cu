@@ -1,0 +1,638 @@
+// fv_batch.cu -- many independent finite-volume problems (instances of any
+// sizes, each with its own dt) advanced by ONE persistent kernel per run of
+// n steps, captured in a CUDA graph.  Each step of each instance is the fused
+// step of fv_step.cuh (same arithmetic, so a batched instance gives the same
+// bits as the instance run alone).
+//
+// Work list.  A run of n steps has n * T tasks (T = warp tasks of all
+// instances for one step), numbered step-major then instance-major.  Warps
+// take tickets from one global counter in increasing order.  Before working
+// on step s of instance i a warp waits until instance i has released step s,
+// i.e. all its tasks of step s - 1 are done: their writes are visible, every
+// read of the buffer step s is about to overwrite is over, and lmax(W^s),
+// hence dt_s, is complete.  The warp that completes the last task of a step
+// advances the instance's t and step, clears the lmax slot two steps ahead
+// and releases the next step.  Tickets are monotone, so a waiting warp only
+// waits on tickets already held by running warps: no deadlock, whatever the
+// number of resident blocks.  Every wait is bounded (%globaltimer); on
+// timeout the kernel raises an abort flag, every warp leaves at its next
+// ticket, and the host reports FV_ERR_TIMEOUT.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/fv.h"
+#include "fv_internal.h"
+#include "fv_step.cuh"
+
+namespace fv {
+
+struct RunCounters {
+  unsigned done;      // tasks of this instance completed during this run
+  unsigned released;  // steps of this instance open during this run (step s needs released >= s)
+};
+
+template <class R> struct BatchArgs {
+  const StepArgs<R> *inst;   // per-instance geometry, buffers, dt policy, BCs
+  Ctrl *ictrl;               // per-instance lmax slots, t, step, error flags
+  RunCounters *rc;           // per-instance counters of this run
+  const int *task_inst;      // T entries: instance of each task of a step
+  const int *task_base;      // first task of each instance within a step
+  unsigned *ticket;          // global ticket counter of this run
+  unsigned *abort;           // set on timeout; every warp leaves
+  int nsteps, T;
+  long long timeout_ns;
+  int skip_release;          // instance whose steps are never released (-1: none)
+};
+
+static __device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+static __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+static __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait (one lane) until *flag >= target; false on timeout or abort.
+static __device__ bool wait_at_least(const unsigned *flag, unsigned target, long long timeout_ns,
+                                     unsigned *abort) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0;; ++it) {
+    if (ld_acquire(flag) >= target) return true;
+    if (ld_acquire(abort) != 0u) return false;
+    if (it > 4) __nanosleep(128);
+    // time limit, plus an iteration cap in case the timer stalls
+    if ((long long)(global_ns() - t0) > timeout_ns || it > (1u << 26)) {
+      atomicOr(abort, kErrTimeout);
+      return false;
+    }
+  }
+}
+
+template <class Sys, class R, int V, int TY, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
+fv_batch_kernel(const BatchArgs<R> b) {
+  __shared__ StepArgs<R> s_args[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  StepArgs<R> &a = s_args[warp];
+  const unsigned total = (unsigned)b.nsteps * (unsigned)b.T;
+  const bool writer = lane >= 1 && lane <= 30;
+  int cur_inst = -1;
+  for (;;) {
+    unsigned t = 0;
+    if (lane == 0) t = ld_acquire(b.abort) ? total : atomicAdd(b.ticket, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= total) break;
+    const unsigned s = t / (unsigned)b.T;
+    const int r = (int)(t - s * (unsigned)b.T);
+    const int i = b.task_inst[r];
+    const int lt = r - b.task_base[i];
+    int ok = 1;
+    if (lane == 0) ok = wait_at_least(&b.rc[i].released, s, b.timeout_ns, b.abort) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) break;
+    if (i != cur_inst) {
+      const unsigned *src = reinterpret_cast<const unsigned *>(&b.inst[i]);
+      unsigned *dstw = reinterpret_cast<unsigned *>(&a);
+      for (int k = lane; k < (int)(sizeof(StepArgs<R>) / 4); k += 32) dstw[k] = __ldg(src + k);
+      __syncwarp();
+      cur_inst = i;
+    }
+    Ctrl *ic = &b.ictrl[i];
+    // dt of this step of instance i (same rule as the single-instance kernel)
+    Ctrl c;
+    c.step = __ldcg(&ic->step);
+    c.t = __ldcg(&ic->t);
+    c.t_end = 0.0;
+    c.err_committed = __ldcg(&ic->err_committed);
+    const double lam = lam_value(__ldcg(&ic->lam[c.step % 3]));
+    double dt = 0.0;
+    unsigned err = 0u;
+    const bool run = choose_dt(a.pol, c, lam, &dt, &err);
+    R lam_loc = (R)0;
+    bool bad = false;
+    const long long n = c.step;
+    if (run) {
+      const R *src = (n & 1) ? a.buf1 : a.buf0;
+      R *dst = (n & 1) ? a.buf0 : a.buf1;
+      const R lx = (R)(dt / a.dx), ly = (R)(dt / a.dy);
+      const int strip = lt % a.nstrips, chunk = lt / a.nstrips;
+      const int X = strip * (30 * V) + (lane - 1) * V;
+      const int y0 = chunk * TY, y1 = min(y0 + TY, a.ny);
+      const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
+      if (xin) march<Sys, R, V, true, true, true>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else march<Sys, R, V, false, true, true>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+    }
+    double l = (double)lam_loc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
+    const int anybad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      if (run) {
+        if (anybad) atomicMax(&ic->lam[(n + 1) % 3], 0x7ff8000000000000ull);
+        else if (l > 0.0) atomicMax(&ic->lam[(n + 1) % 3], lam_bits(l));
+        if (anybad) atomicOr(&ic->err_pending, kErrNonphysical);
+      }
+      if (err) atomicOr(&ic->err_pending, err);
+      __threadfence();
+      const unsigned nt = (unsigned)(a.nstrips * a.nchunks);
+      const unsigned prev = atomicAdd(&b.rc[i].done, 1u);
+      if (prev == (s + 1) * nt - 1) {
+        // last task of step s of instance i: close the step
+        __threadfence();
+        const unsigned e = atomicExch(&ic->err_pending, 0u);
+        if (run) {
+          // L2 reads: another SM wrote these fields during this launch
+          ic->t = __ldcg(&ic->t) + dt;
+          ic->dt_last = dt;
+          ic->step = n + 1;
+          ic->lam[(n + 2) % 3] = 0ull;
+        }
+        if (e) atomicOr(&ic->err_committed, e);
+        __threadfence();
+        if (i != b.skip_release) st_release(&b.rc[i].released, s + 1);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+struct BatchVariant {
+  int system, precision, V, TY, NW;
+  const void *kernel;
+  const char *desc;
+};
+
+#define FV_BVARIANT(SYS, SYSID, R, PREC, V, TY, NW, MB, DESC)                                      \
+  out.push_back(BatchVariant{SYSID, PREC, V, TY, NW,                                              \
+                             reinterpret_cast<const void *>(&fv_batch_kernel<SYS, R, V, TY, NW, MB>), DESC})
+
+static const std::vector<BatchVariant> &batch_variants() {
+  static std::vector<BatchVariant> out;
+  if (out.empty()) {
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, "batch euler f32 v1 ty64 w4 b6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 128, 4, 6, "batch euler f32 v1 ty128 w4 b6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 4, "batch euler f32 v2 ty64 w4 b4");
+    FV_BVARIANT(Euler, kEuler, double, 0, 1, 32, 4, 4, "batch euler f64 v1 ty32 w4 b4");
+    FV_BVARIANT(Advection, kAdvection, double, 0, 1, 32, 4, 4, "batch advection f64 v1 ty32 w4 b4");
+    FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, "batch advection f32 v1 ty64 w4 b6");
+  }
+  return out;
+}
+
+}  // namespace fv
+
+using namespace fv;
+
+struct fv_batch {
+  int n = 0;
+  int system = 0, prec = 0, nvar = 0;
+  size_t esize = 0;
+  std::vector<fv_config> cfg;
+  std::vector<long long> pitch, plane;
+  std::vector<size_t> off;     // byte offset of each instance's first buffer
+  std::vector<size_t> bytes;   // bytes of one buffer of each instance
+  std::vector<double> dx, dy;
+  std::vector<int> has_state;
+  char *arena = nullptr;
+  void *d_args = nullptr;      // StepArgs<R>[n]
+  Ctrl *ictrl = nullptr;
+  Ctrl *h_ictrl = nullptr;
+  unsigned char *runblock = nullptr;  // RunCounters[n] + ticket + abort
+  size_t runblock_bytes = 0;
+  unsigned *h_abort = nullptr;
+  int *task_inst = nullptr, *task_base = nullptr;
+  int T = 0;
+  int variant = -1;
+  int grid = 0;
+  int sms = 0;
+  long long timeout_ns = 2000000000LL;
+  int skip_release = -1;
+  void *staging = nullptr;
+  size_t staging_bytes = 0;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+  std::string err;
+};
+
+static fv_status bfail(fv_batch *b, fv_status s, const std::string &m) {
+  if (b) b->err = m;
+  return s;
+}
+
+#define FV_BCUDA(b, call)                                                                         \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA,                 \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+
+static void bfree_graphs(fv_batch *b) {
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+extern "C" const char *fv_batch_last_error(const fv_batch *b) { return b ? b->err.c_str() : ""; }
+
+extern "C" void fv_batch_destroy(fv_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  bfree_graphs(b);
+  if (b->arena) cudaFree(b->arena);
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->ictrl) cudaFree(b->ictrl);
+  if (b->h_ictrl) cudaFreeHost(b->h_ictrl);
+  if (b->runblock) cudaFree(b->runblock);
+  if (b->h_abort) cudaFreeHost(b->h_abort);
+  if (b->task_inst) cudaFree(b->task_inst);
+  if (b->task_base) cudaFree(b->task_base);
+  if (b->staging) cudaFree(b->staging);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+template <class R>
+static void fill_args(const fv_batch *b, int k, const BatchVariant &V, StepArgs<R> &a) {
+  std::memset(&a, 0, sizeof(a));
+  const fv_config &c = b->cfg[k];
+  a.buf0 = (R *)(b->arena + b->off[k]);
+  a.buf1 = (R *)(b->arena + b->off[k] + b->bytes[k]);
+  a.ctrl = b->ictrl + k;
+  a.nx = c.nx;
+  a.ny = c.ny;
+  a.pitch = b->pitch[k];
+  a.plane = b->plane[k];
+  a.nstrips = (c.nx + 30 * V.V - 1) / (30 * V.V);
+  a.nchunks = (c.ny + V.TY - 1) / V.TY;
+  a.ntasks = a.nstrips * a.nchunks;
+  a.dx = b->dx[k];
+  a.dy = b->dy[k];
+  a.pol.h = a.dx < a.dy ? a.dx : a.dy;
+  a.pol.cfl = c.cfl;
+  a.pol.fixed_dt = c.fixed_dt;
+  a.pol.dt_cap = 1.0e308;
+  if (c.system == FV_ADVECTION) {
+    a.sp.p0 = (R)c.params[0];
+    a.sp.p1 = (R)c.params[1];
+  } else {
+    a.sp.p0 = (R)c.params[0];
+    a.sp.p1 = (R)(c.params[0] - 1.0);
+  }
+  for (int s = 0; s < 4; ++s) {
+    a.bc[s] = c.bc[s];
+    for (int v = 0; v < 8; ++v) a.bc_state[s][v] = (R)c.bc_state[s][v];
+  }
+}
+
+static fv_status batch_select(fv_batch *b, int vi) {
+  const BatchVariant &V = batch_variants()[vi];
+  // per-instance args and the task tables of one step
+  std::vector<int> tinst, tbase(b->n);
+  int T = 0;
+  std::vector<unsigned char> args;
+  const size_t asz = b->prec == 0 ? sizeof(StepArgs<double>) : sizeof(StepArgs<float>);
+  args.resize(asz * b->n);
+  for (int k = 0; k < b->n; ++k) {
+    int nt;
+    if (b->prec == 0) {
+      StepArgs<double> a;
+      fill_args<double>(b, k, V, a);
+      std::memcpy(&args[asz * k], &a, asz);
+      nt = a.ntasks;
+    } else {
+      StepArgs<float> a;
+      fill_args<float>(b, k, V, a);
+      std::memcpy(&args[asz * k], &a, asz);
+      nt = a.ntasks;
+    }
+    tbase[k] = T;
+    for (int q = 0; q < nt; ++q) tinst.push_back(k);
+    T += nt;
+  }
+  if (b->task_inst) cudaFree(b->task_inst);
+  if (b->task_base) cudaFree(b->task_base);
+  b->task_inst = b->task_base = nullptr;
+  FV_BCUDA(b, cudaMalloc(&b->task_inst, sizeof(int) * T));
+  FV_BCUDA(b, cudaMalloc(&b->task_base, sizeof(int) * b->n));
+  FV_BCUDA(b, cudaMemcpy(b->task_inst, tinst.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
+  FV_BCUDA(b, cudaMemcpy(b->task_base, tbase.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
+  FV_BCUDA(b, cudaMemcpy(b->d_args, args.data(), asz * b->n, cudaMemcpyHostToDevice));
+  int nb = 0;
+  FV_BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, 0));
+  if (nb < 1) return bfail(b, FV_ERR_CUDA, "batched kernel cannot launch");
+  b->grid = nb * b->sms;
+  b->T = T;
+  b->variant = vi;
+  bfree_graphs(b);
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out) {
+  if (!out || !cfgs || n < 1) return FV_ERR_INVALID_ARG;
+  *out = nullptr;
+  fv_batch *b = new fv_batch();
+  b->n = n;
+  b->system = cfgs[0].system;
+  b->prec = cfgs[0].precision == FV_F64 ? 0 : 1;
+  b->esize = b->prec == 0 ? 8 : 4;
+  for (int k = 0; k < n; ++k) {
+    const fv_config &c = cfgs[k];
+    if (c.system != cfgs[0].system || c.precision != cfgs[0].precision || c.stream != cfgs[0].stream ||
+        c.tune != cfgs[0].tune) {
+      fv_batch_destroy(b);
+      return FV_ERR_INVALID_ARG;
+    }
+    if (c.system == FV_SPRAY || (c.precision != FV_F64 && c.precision != FV_F32) || c.nx < 1 ||
+        c.ny < 1 || !(c.xmax > c.xmin) || !(c.ymax > c.ymin) || c.npart_x < 1 || c.npart_y < 1 ||
+        c.npart_x > c.nx || c.npart_y > c.ny || (!(c.cfl > 0.0) && !(c.fixed_dt > 0.0)) ||
+        ((c.bc[0] == 0) != (c.bc[2] == 0)) || ((c.bc[1] == 0) != (c.bc[3] == 0)) ||
+        (c.system == FV_EULER && !(c.params[0] > 1.0))) {
+      fv_batch_destroy(b);
+      return FV_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < 4; ++s)
+      if (c.bc[s] < 0 || c.bc[s] > 2) {
+        fv_batch_destroy(b);
+        return FV_ERR_INVALID_ARG;
+      }
+  }
+  b->nvar = b->system == FV_ADVECTION ? 1 : 4;
+  b->cfg.assign(cfgs, cfgs + n);
+  b->stream = (cudaStream_t)cfgs[0].stream;
+  b->has_state.assign(n, 0);
+  size_t total = 0;
+  for (int k = 0; k < n; ++k) {
+    const long long pitch = ((long long)cfgs[k].nx + 31) / 32 * 32;
+    const long long plane = pitch * cfgs[k].ny;
+    const size_t bytes = ((size_t)plane * b->nvar * b->esize + 255) / 256 * 256;
+    b->pitch.push_back(pitch);
+    b->plane.push_back(plane);
+    b->bytes.push_back(bytes);
+    b->off.push_back(total);
+    total += 2 * bytes;
+    b->dx.push_back((cfgs[k].xmax - cfgs[k].xmin) / cfgs[k].nx);
+    b->dy.push_back((cfgs[k].ymax - cfgs[k].ymin) / cfgs[k].ny);
+  }
+  int dev = 0;
+  cudaError_t e;
+  auto bail = [&](cudaError_t e2, const char *what) {
+    fv_batch_destroy(b);
+    (void)what;
+    return e2 == cudaErrorMemoryAllocation ? FV_ERR_OOM : FV_ERR_CUDA;
+  };
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return bail(e, "device");
+  if ((e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return bail(e, "device");
+  if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(e, "stream");
+  if ((e = cudaMalloc(&b->arena, total)) != cudaSuccess) return bail(e, "arena");
+  const size_t asz = b->prec == 0 ? sizeof(StepArgs<double>) : sizeof(StepArgs<float>);
+  if ((e = cudaMalloc(&b->d_args, asz * n)) != cudaSuccess) return bail(e, "args");
+  if ((e = cudaMalloc(&b->ictrl, sizeof(Ctrl) * n)) != cudaSuccess) return bail(e, "ctrl");
+  if ((e = cudaMemset(b->ictrl, 0, sizeof(Ctrl) * n)) != cudaSuccess) return bail(e, "ctrl");
+  if ((e = cudaMallocHost(&b->h_ictrl, sizeof(Ctrl) * n)) != cudaSuccess) return bail(e, "ctrl");
+  b->runblock_bytes = sizeof(RunCounters) * n + 2 * sizeof(unsigned);
+  if ((e = cudaMalloc(&b->runblock, b->runblock_bytes)) != cudaSuccess) return bail(e, "counters");
+  if ((e = cudaMemset(b->runblock, 0, b->runblock_bytes)) != cudaSuccess) return bail(e, "counters");
+  if ((e = cudaMallocHost(&b->h_abort, sizeof(unsigned))) != cudaSuccess) return bail(e, "abort");
+  int vi = -1;
+  const auto &vs = batch_variants();
+  std::vector<int> cand;
+  for (size_t k = 0; k < vs.size(); ++k)
+    if (vs[k].system == b->system && vs[k].precision == b->prec) cand.push_back((int)k);
+  if (cand.empty()) {
+    fv_batch_destroy(b);
+    return FV_ERR_INVALID_ARG;
+  }
+  vi = cand[0];
+  if (cfgs[0].tune >= 2) {
+    if (cfgs[0].tune - 2 >= (int)cand.size()) {
+      fv_batch_destroy(b);
+      return FV_ERR_INVALID_ARG;
+    }
+    vi = cand[cfgs[0].tune - 2];
+  }
+  fv_status st = batch_select(b, vi);
+  if (st != FV_OK) {
+    fv_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return FV_OK;
+}
+
+static fv_status read_ictrl(fv_batch *b) {
+  FV_BCUDA(b, cudaMemcpyAsync(b->h_ictrl, b->ictrl, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  FV_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_set_state(fv_batch *b, int k, const void *src, int src_is_device, int src_dtype,
+                                        int layout) {
+  if (!b) return FV_ERR_INVALID_ARG;
+  if (k < 0 || k >= b->n || !src || (src_dtype != FV_F64 && src_dtype != FV_F32) ||
+      (layout != FV_CONSERVED && layout != FV_PRIMITIVE))
+    return bfail(b, FV_ERR_INVALID_ARG, "bad argument");
+  const fv_config &c = b->cfg[k];
+  const long long ncell = (long long)c.nx * c.ny;
+  const size_t sbytes = (size_t)ncell * b->nvar * (src_dtype == FV_F64 ? 8 : 4);
+  const void *dsrc = src;
+  if (!src_is_device) {
+    if (b->staging_bytes < sbytes) {
+      if (b->staging) {
+        FV_BCUDA(b, cudaStreamSynchronize(b->stream));
+        cudaFree(b->staging);
+        b->staging = nullptr;
+        b->staging_bytes = 0;
+      }
+      FV_BCUDA(b, cudaMalloc(&b->staging, sbytes));
+      b->staging_bytes = sbytes;
+    }
+    FV_BCUDA(b, cudaMemcpyAsync(b->staging, src, sbytes, cudaMemcpyHostToDevice, b->stream));
+    dsrc = b->staging;
+  }
+  // the instance restarts at t = 0, step 0
+  Ctrl h;
+  std::memset(&h, 0, sizeof(h));
+  FV_BCUDA(b, cudaMemcpy(b->ictrl + k, &h, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  void *buf0 = b->arena + b->off[k];
+  FV_BCUDA(b, launch_load_state(b->system, b->prec, dsrc, src_dtype == FV_F32, layout == FV_PRIMITIVE, buf0,
+                                c.nx, c.ny, b->pitch[k], b->plane[k], c.params[0], b->stream));
+  double p0 = c.params[0], p1 = c.params[1];
+  if (b->system == FV_EULER) p1 = c.params[0] - 1.0;
+  FV_BCUDA(b, launch_seed_lambda(b->system, b->prec, buf0, c.nx, c.ny, b->pitch[k], b->plane[k], p0, p1,
+                                 b->ictrl + k, 0, b->stream));
+  FV_BCUDA(b, cudaMemcpyAsync(b->h_ictrl + k, b->ictrl + k, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+  FV_BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (b->h_ictrl[k].err_pending) {
+    std::memset(&h, 0, sizeof(h));
+    FV_BCUDA(b, cudaMemcpy(b->ictrl + k, &h, sizeof(Ctrl), cudaMemcpyHostToDevice));
+    b->has_state[k] = 0;
+    return bfail(b, FV_ERR_NONPHYSICAL, "instance state is not admissible");
+  }
+  b->has_state[k] = 1;
+  return FV_OK;
+}
+
+template <class R>
+static BatchArgs<R> make_batch_args(const fv_batch *b, int nsteps) {
+  BatchArgs<R> a;
+  a.inst = (const StepArgs<R> *)b->d_args;
+  a.ictrl = b->ictrl;
+  a.rc = (RunCounters *)b->runblock;
+  a.task_inst = b->task_inst;
+  a.task_base = b->task_base;
+  a.ticket = (unsigned *)(b->runblock + sizeof(RunCounters) * b->n);
+  a.abort = a.ticket + 1;
+  a.nsteps = nsteps;
+  a.T = b->T;
+  a.timeout_ns = b->timeout_ns;
+  a.skip_release = b->skip_release;
+  return a;
+}
+
+static fv_status batch_graph(fv_batch *b, int nsteps, cudaGraphExec_t *out) {
+  auto it = b->graphs.find(nsteps);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return FV_OK;
+  }
+  if (b->graphs.size() > 8) bfree_graphs(b);
+  const BatchVariant &V = batch_variants()[b->variant];
+  FV_BCUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(b->runblock, 0, b->runblock_bytes, b->cap_stream);
+  if (e == cudaSuccess) {
+    if (b->prec == 0) {
+      BatchArgs<double> a = make_batch_args<double>(b, nsteps);
+      void *args[] = {&a};
+      e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, 0, b->cap_stream);
+    } else {
+      BatchArgs<float> a = make_batch_args<float>(b, nsteps);
+      void *args[] = {&a};
+      e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, 0, b->cap_stream);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bfail(b, FV_ERR_CUDA, std::string("batched graph capture: ") +
+                                     cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  cudaGraphExec_t ge;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, FV_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  b->graphs[nsteps] = ge;
+  *out = ge;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_run(fv_batch *b, int nsteps) {
+  if (!b) return FV_ERR_INVALID_ARG;
+  if (nsteps < 0) return bfail(b, FV_ERR_INVALID_ARG, "nsteps < 0");
+  for (int k = 0; k < b->n; ++k)
+    if (!b->has_state[k]) return bfail(b, FV_ERR_STATE, "an instance has no state");
+  if (nsteps == 0) return FV_OK;
+  // tickets of one run must fit the 32-bit counter
+  if ((unsigned long long)nsteps * (unsigned long long)b->T >= (1ull << 31))
+    return bfail(b, FV_ERR_INVALID_ARG, "too many steps in one run");
+  cudaGraphExec_t g;
+  fv_status st = batch_graph(b, nsteps, &g);
+  if (st != FV_OK) return st;
+  FV_BCUDA(b, cudaGraphLaunch(g, b->stream));
+  FV_BCUDA(b, cudaMemcpyAsync(b->h_abort, b->runblock + sizeof(RunCounters) * b->n + sizeof(unsigned),
+                              sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+  st = read_ictrl(b);
+  if (st != FV_OK) return st;
+  if (*b->h_abort & kErrTimeout) return bfail(b, FV_ERR_TIMEOUT, "a batched-step wait timed out");
+  unsigned all = 0;
+  for (int k = 0; k < b->n; ++k) all |= b->h_ictrl[k].err_committed;
+  if (all & kErrCfl) return bfail(b, FV_ERR_CFL, "an instance's fixed dt violates the CFL condition");
+  if (all & kErrNonphysical) return bfail(b, FV_ERR_NONPHYSICAL, "an instance reached a non-physical state");
+  if (all & kErrZeroSpeed) return bfail(b, FV_ERR_INVALID_ARG, "an instance has lmax = 0");
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_get_state(fv_batch *b, int k, void *dst, int dst_is_device, int dst_dtype) {
+  if (!b) return FV_ERR_INVALID_ARG;
+  if (k < 0 || k >= b->n || !dst || (dst_dtype != FV_F64 && dst_dtype != FV_F32))
+    return bfail(b, FV_ERR_INVALID_ARG, "bad argument");
+  if (!b->has_state[k]) return bfail(b, FV_ERR_STATE, "instance has no state");
+  fv_status st = read_ictrl(b);
+  if (st != FV_OK) return st;
+  const fv_config &c = b->cfg[k];
+  const char *cur = b->arena + b->off[k] + ((b->h_ictrl[k].step & 1) ? b->bytes[k] : 0);
+  const size_t dsz = dst_dtype == FV_F64 ? 8 : 4;
+  const long long ncell = (long long)c.nx * c.ny;
+  if ((dst_dtype == FV_F64) == (b->prec == 0)) {
+    FV_BCUDA(b, cudaMemcpy2DAsync(dst, c.nx * dsz, cur, b->pitch[k] * b->esize, c.nx * dsz,
+                                  (size_t)b->nvar * c.ny,
+                                  dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+  } else {
+    void *target = dst;
+    const size_t need = (size_t)ncell * b->nvar * dsz;
+    if (!dst_is_device) {
+      if (b->staging_bytes < need) {
+        FV_BCUDA(b, cudaStreamSynchronize(b->stream));
+        if (b->staging) cudaFree(b->staging);
+        b->staging = nullptr;
+        b->staging_bytes = 0;
+        FV_BCUDA(b, cudaMalloc(&b->staging, need));
+        b->staging_bytes = need;
+      }
+      target = b->staging;
+    }
+    FV_BCUDA(b, launch_store_state(b->prec, b->nvar, cur, target, dst_dtype == FV_F32, c.nx, c.ny, b->pitch[k],
+                                   b->plane[k], b->stream));
+    if (!dst_is_device)
+      FV_BCUDA(b, cudaMemcpyAsync(dst, b->staging, need, cudaMemcpyDeviceToHost, b->stream));
+  }
+  FV_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_time(fv_batch *b, int k, double *t, long long *step) {
+  if (!b || k < 0 || k >= b->n) return FV_ERR_INVALID_ARG;
+  fv_status st = read_ictrl(b);
+  if (st != FV_OK) return st;
+  if (t) *t = b->h_ictrl[k].t;
+  if (step) *step = b->h_ictrl[k].step;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_kernel_info(fv_batch *b, int *variant, const char **desc) {
+  if (!b) return FV_ERR_INVALID_ARG;
+  const BatchVariant &V = batch_variants()[b->variant];
+  if (variant) {
+    int idx = 0;
+    for (int k = 0; k < b->variant; ++k)
+      if (batch_variants()[k].system == V.system && batch_variants()[k].precision == V.precision) ++idx;
+    *variant = idx;
+  }
+  if (desc) *desc = V.desc;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_set_wait_limit(fv_batch *b, double seconds, int never_release_instance) {
+  if (!b || !(seconds > 0.0) || seconds > 60.0 || never_release_instance < -1 || never_release_instance >= b->n)
+    return FV_ERR_INVALID_ARG;
+  b->timeout_ns = (long long)(seconds * 1e9);
+  b->skip_release = never_release_instance;
+  bfree_graphs(b);
+  return FV_OK;
+}

@@ -308,7 +308,7 @@ static __device__ __forceinline__ void finish_step(Ctrl *ctrl, const StepStart &
     ctrl->blocks_done = 0u;
     const unsigned e = atomicExch(&ctrl->err_pending, 0u) | st.err;
     if (st.run) {
-      ctrl->t = ctrl->t + st.dt;
+      ctrl->t = __ldcg(&ctrl->t) + st.dt;
       ctrl->dt_last = st.dt;
       ctrl->step = n + 1;
       ctrl->lam[(n + 2) % 3] = 0ull;

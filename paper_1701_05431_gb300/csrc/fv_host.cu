@@ -167,7 +167,9 @@ static void free_graphs(fv_ctx *c) {
 static fv_status select_variant(fv_ctx *c, int vi) {
   const Variant &V = all_variants()[vi];
   int nb = 0;
-  FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, 0));
+  if (V.smem > 48 * 1024)
+    FV_CUDA(c, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
+  FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));
   if (nb < 1) return fail(c, FV_ERR_CUDA, std::string("kernel cannot launch: ") + V.desc);
   const int nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
   const int nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
@@ -226,12 +228,12 @@ static fv_status launch_step(fv_ctx *c, cudaStream_t s) {
     StepArgs<double> a = make_args<double>(c, V);
     pol = a.pol;
     void *args[] = {&a};
-    e = cudaLaunchKernel(V.kernel, grid, block, args, 0, s);
+    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
   } else {
     StepArgs<float> a = make_args<float>(c, V);
     pol = a.pol;
     void *args[] = {&a};
-    e = cudaLaunchKernel(V.kernel, grid, block, args, 0, s);
+    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   if (c->cfg.system == FV_SPRAY) {

@@ -18,6 +18,8 @@ struct Variant {
   int TY;          // rows per warp task
   int NW;          // warps per block
   int MINB;        // blocks per SM the register budget is cut for
+  int D;           // TMA ring depth (0: register prefetch only)
+  int smem;        // dynamic shared memory per block (bytes)
   const void *kernel;
   const char *desc;
 };

@@ -287,7 +287,7 @@ cudaError_t launch_spray_source(const SourceLaunch &L, int grid, cudaStream_t s)
 // Transport step kernels of the spray system (the source kernel closes the
 // step, so they run with finalize = 0).
 #define FV_VARIANT(R, PREC, V, TY, NW, MB, DESC)                                                  \
-  out.push_back(Variant{kSpray, PREC, V, TY, NW, MB,                                               \
+  out.push_back(Variant{kSpray, PREC, V, TY, NW, MB, 0, 0,                                         \
                         reinterpret_cast<const void *>(&fv_step_kernel<Spray, R, V, TY, NW, false, MB>), \
                         DESC})
 

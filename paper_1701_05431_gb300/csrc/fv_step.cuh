@@ -41,13 +41,20 @@ template <class R> struct StepArgs {
 };
 
 template <class R, int V> struct VecIO;
+// ld: read-only path (state never written during the launch); ldcg: L2-coherent
+// loads for the persistent batched kernel, whose launch also writes the state.
 template <> struct VecIO<float, 1> {
   static __device__ __forceinline__ void ld(const float *p, float (&o)[1]) { o[0] = __ldg(p); }
+  static __device__ __forceinline__ void ldcg(const float *p, float (&o)[1]) { o[0] = __ldcg(p); }
   static __device__ __forceinline__ void st(float *p, const float (&o)[1]) { __stcs(p, o[0]); }
 };
 template <> struct VecIO<float, 2> {
   static __device__ __forceinline__ void ld(const float *p, float (&o)[2]) {
     float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    o[0] = t.x; o[1] = t.y;
+  }
+  static __device__ __forceinline__ void ldcg(const float *p, float (&o)[2]) {
+    float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
     o[0] = t.x; o[1] = t.y;
   }
   static __device__ __forceinline__ void st(float *p, const float (&o)[2]) {
@@ -59,17 +66,26 @@ template <> struct VecIO<float, 4> {
     float4 t = __ldg(reinterpret_cast<const float4 *>(p));
     o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
   }
+  static __device__ __forceinline__ void ldcg(const float *p, float (&o)[4]) {
+    float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
   static __device__ __forceinline__ void st(float *p, const float (&o)[4]) {
     __stcs(reinterpret_cast<float4 *>(p), make_float4(o[0], o[1], o[2], o[3]));
   }
 };
 template <> struct VecIO<double, 1> {
   static __device__ __forceinline__ void ld(const double *p, double (&o)[1]) { o[0] = __ldg(p); }
+  static __device__ __forceinline__ void ldcg(const double *p, double (&o)[1]) { o[0] = __ldcg(p); }
   static __device__ __forceinline__ void st(double *p, const double (&o)[1]) { __stcs(p, o[0]); }
 };
 template <> struct VecIO<double, 2> {
   static __device__ __forceinline__ void ld(const double *p, double (&o)[2]) {
     double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+    o[0] = t.x; o[1] = t.y;
+  }
+  static __device__ __forceinline__ void ldcg(const double *p, double (&o)[2]) {
+    double2 t = __ldcg(reinterpret_cast<const double2 *>(p));
     o[0] = t.x; o[1] = t.y;
   }
   static __device__ __forceinline__ void st(double *p, const double (&o)[2]) {
@@ -123,7 +139,7 @@ static __device__ __forceinline__ int row_src(const StepArgs<R> &a, int j, int &
   return j;
 }
 
-template <int NV, int V, bool XIN, class R>
+template <int NV, int V, bool XIN, bool CG, class R>
 static __device__ __forceinline__ void load_row(const StepArgs<R> &a, const R *__restrict__ base,
                                                 const LaneCols<V> &L, int j, R (&W)[V][NV]) {
   int dir;
@@ -140,7 +156,8 @@ static __device__ __forceinline__ void load_row(const StepArgs<R> &a, const R *_
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       R t[V];
-      VecIO<R, V>::ld(row + v * a.plane, t);
+      if (CG) VecIO<R, V>::ldcg(row + v * a.plane, t);
+      else VecIO<R, V>::ld(row + v * a.plane, t);
 #pragma unroll
       for (int c = 0; c < V; ++c) W[c][v] = t[c];
     }
@@ -152,7 +169,8 @@ static __device__ __forceinline__ void load_row(const StepArgs<R> &a, const R *_
         for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[L.dir[c]][v];
       } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) W[c][v] = __ldg(row + v * a.plane + L.col[c]);
+        for (int v = 0; v < NV; ++v)
+          W[c][v] = CG ? __ldcg(row + v * a.plane + L.col[c]) : __ldg(row + v * a.plane + L.col[c]);
       }
     }
   }
@@ -205,25 +223,17 @@ template <class R, int V, int NV> struct RowState {
   R dX[V][NV];
 };
 
-// One row of the march: `nxt` receives row j+1 (already prefetched in P),
-// P is refilled with row j+2, the y-face between rows j and j+1 is evaluated
-// once, row j is updated and stored (by the writer lanes), and the new
-// state's wave speed enters the running maximum.
+// Compute part of one row of the march (rows j and j+1 in registers): x-work
+// of row j+1, the y-face between rows j and j+1 evaluated once, update and
+// store of row j (by the writer lanes), and the new state's wave speed.
 template <class Sys, class R, int V, bool XIN, bool FIN>
-static __device__ __forceinline__ void march_row(const StepArgs<R> &a, const R *__restrict__ src,
-                                                 R *__restrict__ dst_lane, const LaneCols<V> &L,
-                                                 int X, int j, int y1, bool writer, R lx, R ly,
-                                                 RowState<R, V, Sys::NV> &cur,
-                                                 RowState<R, V, Sys::NV> &nxt,
-                                                 R (&P)[V][Sys::NV], R (&Fs)[V][Sys::NV],
-                                                 R &lam_loc, bool &bad) {
+static __device__ __forceinline__ void advance_row(const StepArgs<R> &a, R *__restrict__ dst_lane, int X,
+                                                   int j, bool writer, R lx, R ly,
+                                                   RowState<R, V, Sys::NV> &cur,
+                                                   RowState<R, V, Sys::NV> &nxt, R (&Fs)[V][Sys::NV],
+                                                   R &lam_loc, bool &bad) {
   constexpr int NV = Sys::NV;
   using O = Ops<R>;
-#pragma unroll
-  for (int c = 0; c < V; ++c)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) nxt.W[c][v] = P[c][v];
-  if (j + 2 <= y1) load_row<NV, V, XIN>(a, src, L, j + 2, P);
   row_x<Sys, V>(a.sp, nxt.W, nxt.Fy, nxt.sy, nxt.dX);
   R Wn[V][NV];
 #pragma unroll
@@ -268,9 +278,206 @@ static __device__ __forceinline__ void march_row(const StepArgs<R> &a, const R *
   }
 }
 
+// One row of the march with register prefetch: `nxt` receives row j+1
+// (already prefetched in P) and P is refilled with row j+2.
+template <class Sys, class R, int V, bool XIN, bool FIN, bool CG>
+static __device__ __forceinline__ void march_row(const StepArgs<R> &a, const R *__restrict__ src,
+                                                 R *__restrict__ dst_lane, const LaneCols<V> &L,
+                                                 int X, int j, int y1, bool writer, R lx, R ly,
+                                                 RowState<R, V, Sys::NV> &cur,
+                                                 RowState<R, V, Sys::NV> &nxt,
+                                                 R (&P)[V][Sys::NV], R (&Fs)[V][Sys::NV],
+                                                 R &lam_loc, bool &bad) {
+  constexpr int NV = Sys::NV;
+#pragma unroll
+  for (int c = 0; c < V; ++c)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) nxt.W[c][v] = P[c][v];
+  if (j + 2 <= y1) load_row<NV, V, XIN, CG>(a, src, L, j + 2, P);
+  advance_row<Sys, R, V, XIN, FIN>(a, dst_lane, X, j, writer, lx, ly, cur, nxt, Fs, lam_loc, bad);
+}
+
+// ---------------------------------------------------------------- TMA rows
+// Interior strips can stage their rows through shared memory with bulk
+// asynchronous copies (TMA, cp.async.bulk) instead of register prefetch: each
+// warp owns a ring of D row slots, one mbarrier per slot; lane 0 issues, for
+// every variable, one bulk copy of the strip's row segment (widened to 16-byte
+// boundaries), so D rows per warp are in flight without spending registers.
+// A lane reads its V cells of a slot after the slot's barrier completes.
+// Every wait is bounded (%globaltimer); a wait that runs out marks the step
+// with a timeout error and the warp stops waiting (the step is then reported
+// as failed, never silently used).
+
+static __device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+static __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+static __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+static __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+static __device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, unsigned bytes,
+                                                 unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+static __device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+static __device__ __forceinline__ unsigned long long timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <class R> struct TmaGeom {
+  static constexpr int kAlign = 16 / (int)sizeof(R);           // elements per 16 bytes
+  static constexpr __host__ __device__ int seg(int V) { return 32 * V + 2 * kAlign; }  // slot elements per variable
+};
+
+template <class R, int V, int NV, int D> struct RowRing {
+  R *buf;                     // D slots x NV variables x SEG elements
+  unsigned long long *bar;    // D barriers
+  unsigned phase;             // bit k: parity the next wait on slot k expects
+  int seg0;                   // first column of the staged segment (16-byte aligned)
+  int lane_off;               // X - seg0
+  unsigned bytes;             // bytes per variable per row
+  bool broken;
+  static constexpr int SEG = TmaGeom<R>::seg(V);
+};
+
+// Lane 0 stages row j (relative row r of the task) into slot r % D.
+template <class R, int V, int NV, int D>
+static __device__ __forceinline__ void ring_issue(const StepArgs<R> &a, const R *__restrict__ src,
+                                                  RowRing<R, V, NV, D> &rg, int r, int j) {
+  int dir;
+  const int sj = row_src(a, j, dir);
+  if (dir >= 0 || rg.broken) return;  // a prescribed ghost row is not staged
+  if ((threadIdx.x & 31) == 0) {
+    const int slot = r % D;
+    unsigned long long *bar = rg.bar + slot;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, rg.bytes * NV);
+    const R *g = src + (long long)sj * a.pitch + rg.seg0;
+    R *sm = rg.buf + slot * NV * RowRing<R, V, NV, D>::SEG;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) bulk_load(sm + v * RowRing<R, V, NV, D>::SEG, g + v * a.plane, rg.bytes, bar);
+  }
+}
+
+// Every lane takes its V cells of row j (relative row r) out of its slot,
+// then the slot is refilled with relative row r + D (row j + D) if any.
+template <class R, int V, int NV, int D>
+static __device__ __forceinline__ void ring_fetch(const StepArgs<R> &a, const R *__restrict__ src,
+                                                  RowRing<R, V, NV, D> &rg, int r, int j, int nrows,
+                                                  R (&W)[V][NV]) {
+  int dir;
+  row_src(a, j, dir);
+  const int slot = r % D;
+  if (dir >= 0) {
+#pragma unroll
+    for (int c = 0; c < V; ++c)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[dir][v];
+  } else {
+    if (!rg.broken) {
+      const unsigned par = (rg.phase >> slot) & 1u;
+      bool done = mbar_try_wait(rg.bar + slot, par);
+      if (!done) {
+        const unsigned long long t0 = timer_ns();
+        while (!(done = mbar_try_wait(rg.bar + slot, par))) {
+          if (timer_ns() - t0 > 20000000ull) break;  // 20 ms: a staged row never takes that long
+        }
+      }
+      done = __all_sync(0xffffffffu, done);
+      if (!done) {
+        rg.broken = true;
+        if ((threadIdx.x & 31) == 0) atomicOr(&a.ctrl->err_pending, kErrTimeout);
+      }
+      rg.phase ^= 1u << slot;
+    }
+    const R *sm = rg.buf + slot * NV * RowRing<R, V, NV, D>::SEG + rg.lane_off;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < V; ++c) W[c][v] = sm[v * RowRing<R, V, NV, D>::SEG + c];
+  }
+  __syncwarp();
+  if (r + D < nrows) ring_issue<R, V, NV, D>(a, src, rg, r + D, j + D);
+}
+
+// March one interior warp task through the TMA ring.
+template <class Sys, class R, int V, int D, bool FIN>
+static __device__ __forceinline__ void march_tma(const StepArgs<R> &a, const R *__restrict__ src,
+                                                 R *__restrict__ dst, RowRing<R, V, Sys::NV, D> &rg,
+                                                 int X, int y0, int y1, bool writer, R lx, R ly,
+                                                 R &lam_loc, bool &bad) {
+  constexpr int NV = Sys::NV;
+  using O = Ops<R>;
+  // the lanes' cells span [X_0, X_31 + V); stage that span widened to 16 bytes
+  const int x_first = __shfl_sync(0xffffffffu, X, 0);
+  const int x_end = x_first + 32 * V;
+  constexpr int AL = TmaGeom<R>::kAlign;
+  rg.seg0 = x_first / AL * AL;
+  const int seg1 = (x_end + AL - 1) / AL * AL;
+  rg.bytes = (unsigned)((seg1 - rg.seg0) * (int)sizeof(R));
+  rg.lane_off = X - rg.seg0;
+  R *dst_lane = dst + X;
+  const int nrows = y1 - y0 + 2;  // rows y0 - 1 .. y1
+  const int pre = nrows < D ? nrows : D;
+  for (int r = 0; r < pre; ++r) ring_issue<R, V, NV, D>(a, src, rg, r, y0 - 1 + r);
+  RowState<R, V, NV> A, B;
+  R Fs[V][NV];
+  ring_fetch<R, V, NV, D>(a, src, rg, 0, y0 - 1, nrows, A.W);
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    R Fx_[NV], sx_;
+    Sys::fluxes(A.W[c], a.sp, Fx_, sx_, A.Fy[c], A.sy[c]);
+  }
+  ring_fetch<R, V, NV, D>(a, src, rg, 1, y0, nrows, B.W);
+  row_x<Sys, V>(a.sp, B.W, B.Fy, B.sy, B.dX);
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    const R hs = O::mul((R)0.5, O::max(A.sy[c], B.sy[c]));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(A.W[c][v], A.Fy[c][v], B.W[c][v], B.Fy[c][v], hs);
+  }
+  int j = y0;
+  while (true) {
+    if (j >= y1) break;
+    ring_fetch<R, V, NV, D>(a, src, rg, j - y0 + 2, j + 1, nrows, A.W);
+    advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, B, A, Fs, lam_loc, bad);
+    ++j;
+    if (j >= y1) break;
+    ring_fetch<R, V, NV, D>(a, src, rg, j - y0 + 2, j + 1, nrows, B.W);
+    advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, A, B, Fs, lam_loc, bad);
+    ++j;
+  }
+}
+
+// Dynamic shared memory of a block of the TMA variant.
+template <class R, int V, int NV, int D>
+constexpr __host__ __device__ int tma_smem_bytes(int NW) {
+  return NW * (D * NV * TmaGeom<R>::seg(V) * (int)sizeof(R) + D * 8);
+}
+
 // March one warp task: rows [y0, y1) of the strip whose lane l holds the V
 // cells starting at column X.
-template <class Sys, class R, int V, bool XIN, bool FIN>
+template <class Sys, class R, int V, bool XIN, bool FIN, bool CG = false>
 static __device__ __forceinline__ void march(const StepArgs<R> &a, const R *__restrict__ src,
                                              R *__restrict__ dst, int X, int y0, int y1, bool writer,
                                              R lx, R ly, R &lam_loc, bool &bad) {
@@ -283,9 +490,9 @@ static __device__ __forceinline__ void march(const StepArgs<R> &a, const R *__re
   RowState<R, V, NV> A, B;
   R P[V][NV], Fs[V][NV];
   // row below the strip: only its y-fluxes are needed
-  load_row<NV, V, XIN>(a, base, L, y0 - 1, A.W);
-  load_row<NV, V, XIN>(a, base, L, y0, B.W);
-  if (y0 + 1 <= y1) load_row<NV, V, XIN>(a, base, L, y0 + 1, P);
+  load_row<NV, V, XIN, CG>(a, base, L, y0 - 1, A.W);
+  load_row<NV, V, XIN, CG>(a, base, L, y0, B.W);
+  if (y0 + 1 <= y1) load_row<NV, V, XIN, CG>(a, base, L, y0 + 1, P);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
     R Fx_[NV], sx_;
@@ -302,27 +509,45 @@ static __device__ __forceinline__ void march(const StepArgs<R> &a, const R *__re
   int j = y0;
   while (true) {
     if (j >= y1) break;
-    march_row<Sys, R, V, XIN, FIN>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, B, A, P, Fs, lam_loc, bad);
+    march_row<Sys, R, V, XIN, FIN, CG>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, B, A, P, Fs, lam_loc, bad);
     ++j;
     if (j >= y1) break;
-    march_row<Sys, R, V, XIN, FIN>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, A, B, P, Fs, lam_loc, bad);
+    march_row<Sys, R, V, XIN, FIN, CG>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, A, B, P, Fs, lam_loc, bad);
     ++j;
   }
 }
 
 // FIN: this launch also reduces lmax(W^{n+1}) and closes the step (every
 // system but spray, whose source kernel closes the step instead).
-template <class Sys, class R, int V, int TY, int NW, bool FIN = true, int MINB = 1>
+// D > 0: interior strips stage rows through a D-deep TMA ring in shared
+// memory (dynamic shared memory of tma_smem_bytes<R, V, NV, D>(NW) bytes).
+template <class Sys, class R, int V, int TY, int NW, bool FIN = true, int MINB = 1, int D = 0>
 __global__ void __launch_bounds__(NW * 32, MINB)
 fv_step_kernel(const StepArgs<R> a) {
+  constexpr int NV = Sys::NV;
   __shared__ double s_lam[NW];
   __shared__ int s_bad[NW];
   __shared__ StepStart s_st;
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int DD = D > 0 ? D : 1;
+  RowRing<R, V, NV, DD> rg;
+  if (D > 0) {
+    constexpr int slot_bytes = DD * NV * TmaGeom<R>::seg(V) * (int)sizeof(R);
+    unsigned char *mine = s_dyn + warp * (slot_bytes + DD * 8);
+    rg.buf = reinterpret_cast<R *>(mine);
+    rg.bar = reinterpret_cast<unsigned long long *>(mine + slot_bytes);
+    rg.phase = 0u;
+    rg.broken = false;
+    if (lane == 0)
+      for (int k = 0; k < DD; ++k) mbar_init(rg.bar + k, 1);
+    fence_proxy_async();
+    __syncwarp();
+  }
   if (threadIdx.x == 0) s_st = read_step_start(a.pol, a.ctrl);
   __syncthreads();
   const StepStart st = s_st;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
   R lam_loc = (R)0;
   bool bad = false;
 
@@ -343,7 +568,8 @@ fv_step_kernel(const StepArgs<R> a) {
       const int y1 = min(y0 + TY, a.ny);
       // warp-uniform: does every lane of the strip read real columns only?
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
-      if (xin) march<Sys, R, V, true, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      if (D > 0 && xin) march_tma<Sys, R, V, DD, FIN>(a, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (xin) march<Sys, R, V, true, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else march<Sys, R, V, false, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }
   }

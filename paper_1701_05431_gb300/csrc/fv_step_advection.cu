@@ -6,7 +6,7 @@
 namespace fv {
 
 #define FV_VARIANT(R, PREC, V, TY, NW, MB, DESC)                                                     \
-  out.push_back(Variant{kAdvection, PREC, V, TY, NW, MB,                                              \
+  out.push_back(Variant{kAdvection, PREC, V, TY, NW, MB, 0, 0,                                        \
                         reinterpret_cast<const void *>(&fv_step_kernel<Advection, R, V, TY, NW, true, MB>), \
                         DESC})
 

@@ -119,9 +119,10 @@ def _declare_batch(L):
     L.fv_batch_time.restype = ctypes.c_int
     L.fv_batch_last_error.argtypes = [vp]
     L.fv_batch_last_error.restype = ctypes.c_char_p
-    if hasattr(L, "fv_batch_kernel_info"):
-        L.fv_batch_kernel_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_char_p)]
-        L.fv_batch_kernel_info.restype = ctypes.c_int
+    L.fv_batch_kernel_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_char_p)]
+    L.fv_batch_kernel_info.restype = ctypes.c_int
+    L.fv_batch_set_wait_limit.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.fv_batch_set_wait_limit.restype = ctypes.c_int
 
 
 def make_config(d: dict, precision: str = "f64", stream: int = 0, tune: int = 0) -> fv_config:
@@ -287,3 +288,82 @@ def gauss_legendre(Q: int):
     dp = ctypes.POINTER(ctypes.c_double)
     _check(L.fv_gauss_legendre(int(Q), x.ctypes.data_as(dp), w.ctypes.data_as(dp)), None, L)
     return x, w
+
+
+class Batch:
+    """Thin owner of one fv_batch (independent instances, one persistent
+    launch per run); methods map one-to-one onto the fv_batch_* ABI."""
+
+    def __init__(self, problems, precision: str = "f32", stream: int = 0, tune: int = 0):
+        self.lib = load()
+        n = len(problems)
+        arr = (fv_config * n)()
+        for k, d in enumerate(problems):
+            arr[k] = make_config(d, precision, stream, tune)
+        self.shapes = [(NVAR[arr[k].system], arr[k].ny, arr[k].nx) for k in range(n)]
+        h = ctypes.c_void_p()
+        st = self.lib.fv_batch_init(arr, n, ctypes.byref(h))
+        if st != FV_OK:
+            raise FvError(st, "fv_batch_init failed: " + self.lib.fv_status_string(st).decode())
+        self.b = h
+        self.n = n
+
+    def _check(self, st):
+        if st != FV_OK:
+            raise FvError(st, self.lib.fv_batch_last_error(self.b).decode() or
+                          self.lib.fv_status_string(st).decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fv_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, k: int, src, primitive: bool = False, check: bool = True) -> int:
+        p, dev = _ptr(src)
+        st = self.lib.fv_batch_set_state(self.b, int(k), p, dev, _dtype_code(src), 1 if primitive else 0)
+        if check:
+            self._check(st)
+        return st
+
+    def run(self, nsteps: int, check: bool = True) -> int:
+        st = self.lib.fv_batch_run(self.b, int(nsteps))
+        if check:
+            self._check(st)
+        return st
+
+    def get_state(self, k: int, dst):
+        p, dev = _ptr(dst)
+        self._check(self.lib.fv_batch_get_state(self.b, int(k), p, dev, _dtype_code(dst)))
+        return dst
+
+    def state(self, k: int, dtype="float64"):
+        import numpy as np
+        out = np.empty(self.shapes[k], dtype=dtype)
+        return self.get_state(k, out)
+
+    def time(self, k: int):
+        t = ctypes.c_double(0)
+        s = ctypes.c_longlong(0)
+        self._check(self.lib.fv_batch_time(self.b, int(k), ctypes.byref(t), ctypes.byref(s)))
+        return t.value, s.value
+
+    def kernel_info(self):
+        v = ctypes.c_int(0)
+        d = ctypes.c_char_p()
+        self._check(self.lib.fv_batch_kernel_info(self.b, ctypes.byref(v), ctypes.byref(d)))
+        return v.value, d.value.decode()
+
+    def set_wait_limit(self, seconds: float, never_release_instance: int = -1):
+        self._check(self.lib.fv_batch_set_wait_limit(self.b, float(seconds), int(never_release_instance)))
