@@ -182,6 +182,83 @@ def run_reference(args):
     return 0
 
 
+def secondary_workloads(fvlib, torch, sptr, local, hbm):
+    """The other configurations of the hot path, one or two timed jobs each
+    (device-resident inputs, CUDA events around the run calls)."""
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()  # warm-up (also builds the graph)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    # C1: scalar advection 128^2, FP64, 100 steps (latency-bound: 16 K cells)
+    prim, d = wl.advection_bump(128)
+    with fvlib.Solver(d, "f64", stream=sptr) as s:
+        s.set_state(torch.from_numpy(prim).to(f"cuda:{local}"), primitive=True)
+        sec = timed(lambda: s.run(100), 5)
+        out["c1_advection_128_f64"] = {"cell_updates_per_s": 128 * 128 * 100 / sec, "ms_per_job": sec * 1e3,
+                                       "kernel": s.kernel_info()[1]}
+    # C2: four-quadrant Euler 2048^2, 8x8 subdomains, FP64, 500 steps (and FP32)
+    prim, d = wl.four_quadrant(2048, npart=8)
+    pd = torch.from_numpy(prim).to(f"cuda:{local}")
+    for precision in ("f64", "f32"):
+        with fvlib.Solver(d, precision, stream=sptr) as s:
+            def job():
+                s.set_state(pd, primitive=True)
+                s.run(500)
+            sec = timed(job, 1)
+            nb = 2 * 4 * (8 if precision == "f64" else 4) * 2048 * 2048 * 500
+            out[f"c2_four_quadrant_2048_{precision}"] = {
+                "cell_updates_per_s": 2048 * 2048 * 500 / sec, "ms_per_job": sec * 1e3,
+                "hbm_gbs_algorithmic": nb / sec / 1e9, "kernel": s.kernel_info()[1],
+                "note": "job = set_state from device + 500 steps; 134 MB/268 MB state, close to L2 size"}
+    del pd
+    # C4: 512 batched four-quadrant instances, FP32, 200 steps in one persistent launch
+    insts = wl.batched_quadrants(512)
+    ncells = sum(dd["nx"] * dd["ny"] for _, _, dd in insts)
+    with fvlib.Batch([dd for _, _, dd in insts], "f32", stream=sptr) as b:
+        for k, (_, pr, _) in enumerate(insts):
+            b.set_state(k, pr, primitive=True)
+        del insts
+        sec = timed(lambda: b.run(200), 2)
+        nb = 2 * 4 * 4 * ncells * 200
+        out["c4_batched_512_f32"] = {"cell_updates_per_s": ncells * 200 / sec, "ms_per_job": sec * 1e3,
+                                     "cells": ncells, "hbm_gbs_algorithmic": nb / sec / 1e9,
+                                     "hbm_frac": nb / sec / 1e9 / hbm, "kernel": b.kernel_info()[1],
+                                     "launches_per_job": 1}
+    # C5: spray moments 2048^2, periodic, 200 steps; FP64 plain and FP32-bulk
+    prim, d = wl.spray_field(2048)
+    pd = torch.from_numpy(prim).to(f"cuda:{local}")
+    for precision in ("f64", "f32"):
+        with fvlib.Solver(d, precision, stream=sptr) as s:
+            s.set_state(pd, primitive=True)
+            s.run(2)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run(200)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            out[f"c5_spray_2048_{precision}"] = {
+                "cell_updates_per_s": 2048 * 2048 * 200 / sec, "ms_per_job": sec * 1e3,
+                "kernel": s.kernel_info()[1],
+                "bound": "fp64 pipe (maximum-entropy Newton in FP64 in both precisions)"}
+    del pd
+    return out
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +269,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other configurations")
     ap.add_argument("--tune", type=int, default=0)
     ap.add_argument("--only", choices=["f32", "f64"], default=None,
                     help="time one precision only (profiling runs)")
@@ -282,7 +360,7 @@ def main():
 
     # ---- FP64 plain beside it
     if args.only == "f32":
-        args.no_fp64 = args.no_e2e = args.no_cpu_baseline = True
+        args.no_fp64 = args.no_e2e = args.no_cpu_baseline = args.no_extra = True
     if not args.no_fp64:
         k64 = max(1, min(args.steps, 2))
         ms64, _, kinfo64 = time_jobs("f64", k64, 1)
@@ -294,7 +372,7 @@ def main():
                        "hbm_gbs_achieved": algo64 / avg64 / 1e9, "hbm_frac": algo64 / avg64 / 1e9 / hbm,
                        "note": "FP64 arithmetic is bound by the FP64 pipe, not HBM"}
         out["fp32_speedup_vs_fp64"] = value32 / value64
-        out["gpu_launches"] += k64 * nsteps_job
+        out["fp64"]["gpu_launches"] = k64 * nsteps_job
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
@@ -324,7 +402,7 @@ def main():
                       "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4),
                       "wall_s": wall, "steps": k,
                       "path": "fv_set_state(pinned host f32 primitive) + fv_run + fv_get_state(pinned host f32)"}
-        out["gpu_launches"] += k * (nsteps_job + 2)
+        out["e2e"]["gpu_launches"] = k * (nsteps_job + 2)
 
     # ---- accuracy of the timed configuration against stored oracle samples
     golden = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle_samples.npz")
@@ -344,6 +422,9 @@ def main():
             linf = (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).tolist()
             acc[precision] = {"rel_l1": l1, "rel_linf": linf}
         out["accuracy_vs_oracle"] = dict(acc, samples=int(len(g["flat_index"])), steps=int(g["steps"]))
+
+    if not args.no_extra and args.workload == "c3":
+        out["other_workloads"] = secondary_workloads(fvlib, torch, sptr, local, hbm)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline_run(args.workload, d, prim)
