@@ -469,6 +469,160 @@ static __device__ __forceinline__ void march_tma(const StepArgs<R> &a, const R *
   }
 }
 
+// ---------------------------------------------------------------- cp.async rows
+// Second staging scheme for interior strips: every lane copies its own V
+// cells of a row into its own slot of a per-warp ring in shared memory with
+// cp.async (each lane later reads only what it copied, so no cross-lane
+// synchronisation is needed); D - 1 rows stay in flight per lane.
+
+static __device__ __forceinline__ void cp_async_bytes4(void *sdst, const void *gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+static __device__ __forceinline__ void cp_async_bytes8(void *sdst, const void *gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+static __device__ __forceinline__ void cp_async_bytes16(void *sdst, const void *gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+static __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <class R, int V>
+static __device__ __forceinline__ void cp_async_cells(R *sdst, const R *gsrc) {
+  constexpr int B = V * (int)sizeof(R);
+  if (B == 4) cp_async_bytes4(sdst, gsrc);
+  else if (B == 8) cp_async_bytes8(sdst, gsrc);
+  else if (B == 16) cp_async_bytes16(sdst, gsrc);
+  else {
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+      if (sizeof(R) == 8) cp_async_bytes8(sdst + c, gsrc + c);
+      else cp_async_bytes4(sdst + c, gsrc + c);
+    }
+  }
+}
+
+template <class R, int V, int NV, int D> struct LaneRing {
+  R *buf;  // this lane's D slots x NV variables x V cells, lane-interleaved
+};
+
+// Lane-private slot address of (slot, variable): lanes are interleaved so a
+// warp's copies of one variable land in one contiguous 32 * V span.
+template <class R, int V, int NV, int D>
+static __device__ __forceinline__ R *lane_slot(const LaneRing<R, V, NV, D> &rg, int slot, int v) {
+  return rg.buf + ((slot * NV + v) * 32) * V;
+}
+
+template <class R, int V, int NV, int D>
+static __device__ __forceinline__ void lring_issue(const StepArgs<R> &a, const R *__restrict__ src_lane,
+                                                   const LaneRing<R, V, NV, D> &rg, int r, int j) {
+  int dir;
+  const int sj = row_src(a, j, dir);
+  const int slot = r % D;
+  if (dir >= 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < V; ++c) lane_slot(rg, slot, v)[c] = a.bc_state[dir][v];
+  } else {
+    const R *g = src_lane + (long long)sj * a.pitch;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cp_async_cells<R, V>(lane_slot(rg, slot, v), g + v * a.plane);
+  }
+  cp_async_commit();
+}
+
+template <class R, int V, int NV, int D>
+static __device__ __forceinline__ void lring_read(const LaneRing<R, V, NV, D> &rg, int r, R (&W)[V][NV]) {
+  const int slot = r % D;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    R t[V];
+    const R *p = lane_slot(rg, slot, v);
+#pragma unroll
+    for (int c = 0; c < V; ++c) t[c] = p[c];
+#pragma unroll
+    for (int c = 0; c < V; ++c) W[c][v] = t[c];
+  }
+}
+
+// March one interior warp task through the per-lane cp.async ring.  Rows
+// are numbered r = 0 .. nrows - 1 (row y0 - 1 + r); before reading row r the
+// lane has issued rows up to r + D - 2 and waits until at most D - 2 copy
+// groups are pending, i.e. row r has landed.  A slot is refilled only after
+// the row read from it has been consumed by the flux computation.
+template <class Sys, class R, int V, int D, bool FIN>
+static __device__ __forceinline__ void march_async(const StepArgs<R> &a, const R *__restrict__ src,
+                                                   R *__restrict__ dst, const LaneRing<R, V, Sys::NV, D> &rg,
+                                                   int X, int y0, int y1, bool writer, R lx, R ly,
+                                                   R &lam_loc, bool &bad) {
+  constexpr int NV = Sys::NV;
+  using O = Ops<R>;
+  const R *src_lane = src + X;
+  R *dst_lane = dst + X;
+  const int nrows = y1 - y0 + 2;
+  // prologue: rows 0 .. D-2 in flight (empty groups past the end keep the count)
+#pragma unroll
+  for (int r = 0; r < D - 1; ++r) {
+    if (r < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, r, y0 - 1 + r);
+    else cp_async_commit();
+  }
+  RowState<R, V, NV> A, B;
+  R Fs[V][NV];
+  cp_async_wait<D - 2>();
+  lring_read<R, V, NV, D>(rg, 0, A.W);
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    R Fx_[NV], sx_;
+    Sys::fluxes(A.W[c], a.sp, Fx_, sx_, A.Fy[c], A.sy[c]);
+  }
+  if (D - 1 < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, D - 1, y0 - 1 + D - 1);
+  else cp_async_commit();
+  cp_async_wait<D - 2>();
+  lring_read<R, V, NV, D>(rg, 1, B.W);
+  row_x<Sys, V>(a.sp, B.W, B.Fy, B.sy, B.dX);
+  if (D < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, D, y0 - 1 + D);
+  else cp_async_commit();
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    const R hs = O::mul((R)0.5, O::max(A.sy[c], B.sy[c]));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(A.W[c][v], A.Fy[c][v], B.W[c][v], B.Fy[c][v], hs);
+  }
+  int j = y0;
+  while (true) {
+    if (j >= y1) break;
+    {
+      const int r = j - y0 + 2;
+      cp_async_wait<D - 2>();
+      lring_read<R, V, NV, D>(rg, r, A.W);
+      advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, B, A, Fs, lam_loc, bad);
+      if (r + D - 1 < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
+      else cp_async_commit();
+    }
+    ++j;
+    if (j >= y1) break;
+    {
+      const int r = j - y0 + 2;
+      cp_async_wait<D - 2>();
+      lring_read<R, V, NV, D>(rg, r, B.W);
+      advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, A, B, Fs, lam_loc, bad);
+      if (r + D - 1 < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
+      else cp_async_commit();
+    }
+    ++j;
+  }
+  cp_async_wait<0>();
+}
+
+template <class R, int V, int NV, int D>
+constexpr __host__ __device__ int async_smem_bytes(int NW) {
+  return NW * D * NV * 32 * V * (int)sizeof(R);
+}
+
 // Dynamic shared memory of a block of the TMA variant.
 template <class R, int V, int NV, int D>
 constexpr __host__ __device__ int tma_smem_bytes(int NW) {
@@ -521,6 +675,8 @@ static __device__ __forceinline__ void march(const StepArgs<R> &a, const R *__re
 // system but spray, whose source kernel closes the step instead).
 // D > 0: interior strips stage rows through a D-deep TMA ring in shared
 // memory (dynamic shared memory of tma_smem_bytes<R, V, NV, D>(NW) bytes).
+// D < 0: interior strips stage rows through a per-lane cp.async ring of
+// depth -D (dynamic shared memory of async_smem_bytes<R, V, NV, -D>(NW)).
 template <class Sys, class R, int V, int TY, int NW, bool FIN = true, int MINB = 1, int D = 0>
 __global__ void __launch_bounds__(NW * 32, MINB)
 fv_step_kernel(const StepArgs<R> a) {
@@ -532,7 +688,10 @@ fv_step_kernel(const StepArgs<R> a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int DD = D > 0 ? D : 1;
+  constexpr int DA = D < 0 ? -D : 2;
   RowRing<R, V, NV, DD> rg;
+  LaneRing<R, V, NV, DA> lrg;
+  if (D < 0) lrg.buf = reinterpret_cast<R *>(s_dyn) + warp * (DA * NV * 32 * V) + lane * V;
   if (D > 0) {
     constexpr int slot_bytes = DD * NV * TmaGeom<R>::seg(V) * (int)sizeof(R);
     unsigned char *mine = s_dyn + warp * (slot_bytes + DD * 8);
@@ -569,6 +728,7 @@ fv_step_kernel(const StepArgs<R> a) {
       // warp-uniform: does every lane of the strip read real columns only?
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
       if (D > 0 && xin) march_tma<Sys, R, V, DD, FIN>(a, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (D < 0 && xin) march_async<Sys, R, V, DA, FIN>(a, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else if (xin) march<Sys, R, V, true, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else march<Sys, R, V, false, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }

@@ -7,16 +7,23 @@
 
 namespace fv {
 
-#define FV_VARIANT(R, PREC, V, TY, NW, MB, D, DESC)                                                 \
-  out.push_back(Variant{kEuler, PREC, V, TY, NW, MB, D, (D) > 0 ? tma_smem_bytes<R, V, 4, (D > 0 ? D : 1)>(NW) : 0, \
+#define FV_VARIANT(R, PREC, V, TY, NW, MB, D, DESC)                                                   \
+  out.push_back(Variant{kEuler, PREC, V, TY, NW, MB, D,                                                 \
+                        (D) > 0 ? tma_smem_bytes<R, V, 4, (D > 0 ? D : 1)>(NW)                          \
+                                : (D) < 0 ? async_smem_bytes<R, V, 4, (D < 0 ? -D : 1)>(NW) : 0,         \
                         reinterpret_cast<const void *>(&fv_step_kernel<Euler, R, V, TY, NW, true, MB, D>), DESC})
 
 void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT(double, 0, 1, 64, 4, 1, 0, "euler f64 v1 ty64 w4");
   FV_VARIANT(double, 0, 1, 32, 4, 1, 0, "euler f64 v1 ty32 w4");
   FV_VARIANT(double, 0, 1, 64, 4, 4, 4, "euler f64 v1 ty64 w4 b4 tma4");
+  FV_VARIANT(double, 0, 1, 64, 4, 4, -4, "euler f64 v1 ty64 w4 b4 async4");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 0, "euler f32 v2 ty64 w4 b5");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 4, "euler f32 v2 ty64 w4 b5 tma4");
+  FV_VARIANT(float, 1, 2, 64, 4, 5, -4, "euler f32 v2 ty64 w4 b5 async4");
+  FV_VARIANT(float, 1, 2, 64, 4, 5, -6, "euler f32 v2 ty64 w4 b5 async6");
+  FV_VARIANT(float, 1, 1, 64, 4, 8, -6, "euler f32 v1 ty64 w4 b8 async6");
+  FV_VARIANT(float, 1, 1, 64, 8, 4, -8, "euler f32 v1 ty64 w8 b4 async8");
   FV_VARIANT(float, 1, 2, 64, 4, 4, 6, "euler f32 v2 ty64 w4 b4 tma6");
   FV_VARIANT(float, 1, 2, 128, 4, 5, 8, "euler f32 v2 ty128 w4 b5 tma8");
   FV_VARIANT(float, 1, 1, 64, 4, 6, 6, "euler f32 v1 ty64 w4 b6 tma6");
