@@ -16,21 +16,19 @@ namespace fv {
 void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT(double, 0, 1, 64, 4, 1, 0, "euler f64 v1 ty64 w4");
   FV_VARIANT(double, 0, 1, 32, 4, 1, 0, "euler f64 v1 ty32 w4");
-  FV_VARIANT(double, 0, 1, 64, 4, 4, 4, "euler f64 v1 ty64 w4 b4 tma4");
   FV_VARIANT(double, 0, 1, 64, 4, 4, -4, "euler f64 v1 ty64 w4 b4 async4");
+  FV_VARIANT(float, 1, 2, 64, 4, 5, -6, "euler f32 v2 ty64 w4 b5 async6");
+  FV_VARIANT(float, 1, 2, 64, 4, 5, -4, "euler f32 v2 ty64 w4 b5 async4");
+  FV_VARIANT(float, 1, 2, 64, 4, 5, -8, "euler f32 v2 ty64 w4 b5 async8");
+  FV_VARIANT(float, 1, 2, 64, 4, 4, -6, "euler f32 v2 ty64 w4 b4 async6");
+  FV_VARIANT(float, 1, 2, 64, 4, 4, -8, "euler f32 v2 ty64 w4 b4 async8");
+  FV_VARIANT(float, 1, 2, 128, 4, 5, -6, "euler f32 v2 ty128 w4 b5 async6");
+  FV_VARIANT(float, 1, 2, 32, 4, 5, -6, "euler f32 v2 ty32 w4 b5 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 0, "euler f32 v2 ty64 w4 b5");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 4, "euler f32 v2 ty64 w4 b5 tma4");
-  FV_VARIANT(float, 1, 2, 64, 4, 5, -4, "euler f32 v2 ty64 w4 b5 async4");
-  FV_VARIANT(float, 1, 2, 64, 4, 5, -6, "euler f32 v2 ty64 w4 b5 async6");
-  FV_VARIANT(float, 1, 1, 64, 4, 8, -6, "euler f32 v1 ty64 w4 b8 async6");
-  FV_VARIANT(float, 1, 1, 64, 8, 4, -8, "euler f32 v1 ty64 w8 b4 async8");
   FV_VARIANT(float, 1, 2, 64, 4, 4, 6, "euler f32 v2 ty64 w4 b4 tma6");
-  FV_VARIANT(float, 1, 2, 128, 4, 5, 8, "euler f32 v2 ty128 w4 b5 tma8");
-  FV_VARIANT(float, 1, 1, 64, 4, 6, 6, "euler f32 v1 ty64 w4 b6 tma6");
-  FV_VARIANT(float, 1, 1, 64, 4, 8, 4, "euler f32 v1 ty64 w4 b8 tma4");
   FV_VARIANT(float, 1, 1, 64, 4, 8, 0, "euler f32 v1 ty64 w4 b8");
-  FV_VARIANT(float, 1, 1, 128, 8, 4, 8, "euler f32 v1 ty128 w8 b4 tma8");
-  FV_VARIANT(float, 1, 2, 64, 4, 1, 0, "euler f32 v2 ty64 w4");
+  FV_VARIANT(float, 1, 1, 64, 4, 8, -6, "euler f32 v1 ty64 w4 b8 async6");
 }
 
 }  // namespace fv
