@@ -139,9 +139,9 @@ __global__ void seed_lambda_kernel(const R *__restrict__ state, int nx, int ny, 
     R W[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) W[v] = state[v * plane + o];
-    bool b;
+    unsigned b;
     R lc = Sys::lambda(W, P, b);
-    bad |= b;
+    bad |= b != 0u;
     l = fmax(l, (double)lc);
   }
 #pragma unroll

@@ -123,23 +123,24 @@ fv_batch_kernel(const BatchArgs<R> b) {
     unsigned err = 0u;
     const bool run = choose_dt(a.pol, c, lam, &dt, &err);
     R lam_loc = (R)0;
-    bool bad = false;
+    unsigned bad = 0u;
     const long long n = c.step;
     if (run) {
       const R *src = (n & 1) ? a.buf1 : a.buf0;
       R *dst = (n & 1) ? a.buf0 : a.buf1;
+      const SysParams<R> P = a.sp;
       const R lx = (R)(dt / a.dx), ly = (R)(dt / a.dy);
       const int strip = lt % a.nstrips, chunk = lt / a.nstrips;
       const int X = strip * (30 * V) + (lane - 1) * V;
       const int y0 = chunk * TY, y1 = min(y0 + TY, a.ny);
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
-      if (xin) march<Sys, R, V, true, true, true>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else march<Sys, R, V, false, true, true>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      if (xin) march<Sys, R, V, true, true, true>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else march<Sys, R, V, false, true, true>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }
     double l = (double)lam_loc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
-    const int anybad = __any_sync(0xffffffffu, bad);
+    const int anybad = __any_sync(0xffffffffu, bad != 0u);
     if (lane == 0) {
       if (run) {
         if (anybad) atomicMax(&ic->lam[(n + 1) % 3], 0x7ff8000000000000ull);

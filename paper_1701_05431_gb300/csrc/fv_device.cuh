@@ -39,7 +39,23 @@ struct Ctrl {
 
 template <class R> struct Ops;
 
+// Every arithmetic type A used by the kernels provides:
+//   S        storage type of one cell value (float or double)
+//   K        cells packed in one A (1, or 2 for F2)
+//   add/sub/mul/fma/rcp/sqrt/abs/max/neg   per component, explicitly rounded
+//   splat(s), pack(p), unpack(x, p)        conversions to and from storage
+//   shfl_up/shfl_down                      warp shuffles of whole values
+//   shift_in(prev, cur)   the values one cell to the west of `cur`, given the
+//                         value `prev` that precedes `cur` (K = 1: prev;
+//                         K = 2: (prev.y, cur.x))
+//   shift_out(cur, next)  the values one cell to the east of `cur`
+//   not_pos(x), not_fin(x)  bit k set when component k is not > 0 / not a
+//                         finite value below 3e38
+//   hmax(x, mask)         largest component among those selected by mask
+
 template <> struct Ops<double> {
+  using S = double;
+  static constexpr int K = 1;
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
@@ -49,9 +65,21 @@ template <> struct Ops<double> {
   static __device__ __forceinline__ double abs(double a) { return fabs(a); }
   static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
   static __device__ __forceinline__ double neg(double a) { return -a; }
+  static __device__ __forceinline__ double splat(double s) { return s; }
+  static __device__ __forceinline__ double pack(const double *p) { return p[0]; }
+  static __device__ __forceinline__ void unpack(double x, double *p) { p[0] = x; }
+  static __device__ __forceinline__ double shfl_up(double x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
+  static __device__ __forceinline__ double shfl_down(double x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
+  static __device__ __forceinline__ double shift_in(double prev, double) { return prev; }
+  static __device__ __forceinline__ double shift_out(double, double next) { return next; }
+  static __device__ __forceinline__ unsigned not_pos(double x) { return (x > 0.0) ? 0u : 1u; }
+  static __device__ __forceinline__ unsigned not_fin(double x) { return (fabs(x) <= 3.0e38) ? 0u : 1u; }
+  static __device__ __forceinline__ double hmax(double x, unsigned mask) { return (mask & 1u) ? x : 0.0; }
 };
 
 template <> struct Ops<float> {
+  using S = float;
+  static constexpr int K = 1;
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
@@ -72,6 +100,87 @@ template <> struct Ops<float> {
   static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
   static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
   static __device__ __forceinline__ float neg(float a) { return -a; }
+  static __device__ __forceinline__ float splat(float s) { return s; }
+  static __device__ __forceinline__ float pack(const float *p) { return p[0]; }
+  static __device__ __forceinline__ void unpack(float x, float *p) { p[0] = x; }
+  static __device__ __forceinline__ float shfl_up(float x, int d) { return __shfl_up_sync(0xffffffffu, x, d); }
+  static __device__ __forceinline__ float shfl_down(float x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
+  static __device__ __forceinline__ float shift_in(float prev, float) { return prev; }
+  static __device__ __forceinline__ float shift_out(float, float next) { return next; }
+  static __device__ __forceinline__ unsigned not_pos(float x) { return (x > 0.0f) ? 0u : 1u; }
+  static __device__ __forceinline__ unsigned not_fin(float x) { return (fabsf(x) <= 3.0e38f) ? 0u : 1u; }
+  static __device__ __forceinline__ float hmax(float x, unsigned mask) { return (mask & 1u) ? x : 0.0f; }
+};
+
+// Two adjacent cells of one variable in one 64-bit register pair.  add, sub,
+// mul and fma use Blackwell's packed FP32x2 instructions (one instruction for
+// both cells, each component rounded exactly like the scalar instruction), so
+// a kernel on F2 gives the same bits as the scalar FP32 kernel.
+struct __align__(8) F2 {
+  float x, y;
+};
+
+template <> struct Ops<F2> {
+  using S = float;
+  static constexpr int K = 2;
+  static __device__ __forceinline__ unsigned long long b(F2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+  }
+  static __device__ __forceinline__ F2 f(unsigned long long r) {
+    F2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+  }
+  static __device__ __forceinline__ F2 add(F2 a, F2 c) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b(a)), "l"(b(c)));
+    return f(d);
+  }
+  static __device__ __forceinline__ F2 sub(F2 a, F2 c) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b(a)), "l"(b(c)));
+    return f(d);
+  }
+  static __device__ __forceinline__ F2 mul(F2 a, F2 c) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b(a)), "l"(b(c)));
+    return f(d);
+  }
+  static __device__ __forceinline__ F2 fma(F2 a, F2 c, F2 e) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(b(a)), "l"(b(c)), "l"(b(e)));
+    return f(d);
+  }
+  static __device__ __forceinline__ F2 rcp(F2 a) { return F2{Ops<float>::rcp(a.x), Ops<float>::rcp(a.y)}; }
+  static __device__ __forceinline__ F2 sqrt(F2 a) { return F2{Ops<float>::sqrt(a.x), Ops<float>::sqrt(a.y)}; }
+  static __device__ __forceinline__ F2 abs(F2 a) { return F2{fabsf(a.x), fabsf(a.y)}; }
+  static __device__ __forceinline__ F2 max(F2 a, F2 c) { return F2{fmaxf(a.x, c.x), fmaxf(a.y, c.y)}; }
+  static __device__ __forceinline__ F2 neg(F2 a) { return F2{-a.x, -a.y}; }
+  static __device__ __forceinline__ F2 splat(float s) { return F2{s, s}; }
+  static __device__ __forceinline__ F2 pack(const float *p) { return F2{p[0], p[1]}; }
+  static __device__ __forceinline__ void unpack(F2 a, float *p) {
+    p[0] = a.x;
+    p[1] = a.y;
+  }
+  static __device__ __forceinline__ F2 shfl_up(F2 a, int d) {
+    return F2{__shfl_up_sync(0xffffffffu, a.x, d), __shfl_up_sync(0xffffffffu, a.y, d)};
+  }
+  static __device__ __forceinline__ F2 shfl_down(F2 a, int d) {
+    return F2{__shfl_down_sync(0xffffffffu, a.x, d), __shfl_down_sync(0xffffffffu, a.y, d)};
+  }
+  static __device__ __forceinline__ F2 shift_in(F2 prev, F2 cur) { return F2{prev.y, cur.x}; }
+  static __device__ __forceinline__ F2 shift_out(F2 cur, F2 next) { return F2{cur.y, next.x}; }
+  static __device__ __forceinline__ unsigned not_pos(F2 a) {
+    return ((a.x > 0.0f) ? 0u : 1u) | ((a.y > 0.0f) ? 0u : 2u);
+  }
+  static __device__ __forceinline__ unsigned not_fin(F2 a) {
+    return ((fabsf(a.x) <= 3.0e38f) ? 0u : 1u) | ((fabsf(a.y) <= 3.0e38f) ? 0u : 2u);
+  }
+  static __device__ __forceinline__ float hmax(F2 a, unsigned mask) {
+    return fmaxf((mask & 1u) ? a.x : 0.0f, (mask & 2u) ? a.y : 0.0f);
+  }
 };
 
 // Parameters of the system, in the arithmetic precision.
@@ -79,12 +188,17 @@ template <class R> struct SysParams {
   R p0, p1;   // advection: a_x, a_y | Euler: gamma, gamma - 1 | spray: unused
 };
 
+template <class A>
+static __device__ __forceinline__ SysParams<A> splat_params(const SysParams<typename Ops<A>::S> &p) {
+  return SysParams<A>{Ops<A>::splat(p.p0), Ops<A>::splat(p.p1)};
+}
+
 // ---------------------------------------------------------------- systems
 // Each system provides, for one cell W:
 //   fluxes(): F(W).(1,0), the largest |eigenvalue| along x, F(W).(0,1) and
 //             the largest |eigenvalue| along y;
-//   lambda(): max of the two (the cell's term of Eq. (CFL_cond)) and whether
-//             the state is admissible.
+//   lambda(): max of the two (the cell's term of Eq. (CFL_cond)) and, per
+//             packed cell, a bit set when the state is not admissible.
 
 // Scalar advection, F = a u: eigenvalue a.n.
 struct Advection {
@@ -99,10 +213,10 @@ struct Advection {
     sy = O::abs(P.p1);
   }
   template <class R>
-  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, bool &bad) {
+  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, unsigned &bad) {
     using O = Ops<R>;
     R l = O::max(O::abs(P.p0), O::abs(P.p1));
-    bad = !(W[0] == W[0]) || !(O::abs(W[0]) <= (R)3.0e38);
+    bad = O::not_fin(W[0]);
     return l;
   }
 };
@@ -120,7 +234,7 @@ struct Euler {
     u = O::mul(W[1], inv);
     v = O::mul(W[2], inv);
     // kinetic energy: a plain sum of two rounded products keeps x <-> y symmetry
-    R ke = O::mul((R)0.5, O::add(O::mul(W[1], u), O::mul(W[2], v)));
+    R ke = O::mul(O::splat(0.5), O::add(O::mul(W[1], u), O::mul(W[2], v)));
     p = O::mul(P.p1, O::sub(W[3], ke));
     c = O::sqrt(O::mul(O::mul(P.p0, p), inv));
   }
@@ -143,12 +257,12 @@ struct Euler {
     sy = O::add(O::abs(v), c);
   }
   template <class R>
-  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, bool &bad) {
+  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, unsigned &bad) {
     using O = Ops<R>;
     R u, v, p, c;
     prims(W, P, u, v, p, c);
     R l = O::add(O::max(O::abs(u), O::abs(v)), c);
-    bad = !(W[0] > (R)0) || !(p > (R)0) || !(l <= (R)3.0e38);
+    bad = O::not_pos(W[0]) | O::not_pos(p) | O::not_fin(l);
     return l;
   }
 };
@@ -173,7 +287,8 @@ struct Spray {
     sy = O::abs(v);
   }
   template <class R>
-  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, bool &bad) {
+  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, unsigned &bad) {
+    static_assert(Ops<R>::K == 1, "spray cells are not packed");
     using O = Ops<R>;
     R inv = O::rcp(W[2]);
     R u = O::mul(W[4], inv);
@@ -185,7 +300,7 @@ struct Spray {
     const bool inside = c0 > 0.0 && c1 > 0.0 && c0 - c1 > 0.0 && c0 * c2 - c1 * c1 > 0.0 &&
                         c1 - c2 > 0.0 && c1 * c3 - c2 * c2 > 0.0 &&
                         (c0 - c1) * (c2 - c3) - (c1 - c2) * (c1 - c2) > 0.0;
-    bad = !inside || !(l <= (R)3.0e38);
+    bad = (!inside || !(l <= (R)3.0e38)) ? 1u : 0u;
     return l;
   }
 };
@@ -195,7 +310,7 @@ struct Spray {
 template <class R>
 static __device__ __forceinline__ R lf_face(R WL, R FL, R WR, R FR, R hs) {
   using O = Ops<R>;
-  return O::fma(O::neg(hs), O::sub(WR, WL), O::mul((R)0.5, O::add(FL, FR)));
+  return O::fma(O::neg(hs), O::sub(WR, WL), O::mul(O::splat(0.5), O::add(FL, FR)));
 }
 
 // Residual and forward-Euler update of Eq. (VF_scheme) for one variable:

@@ -221,9 +221,9 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
         const double c[4] = {(double)wn[0], (double)wn[1], (double)wn[2], (double)wn[3]};
         cell_bad = !realizable(c);
         SysParams<R> P{(R)0, (R)0};
-        bool b;
+        unsigned b;
         const R l = Spray::lambda<R>(wn, P, b);
-        cell_bad |= b;
+        cell_bad |= b != 0u;
         lmax = fmax(lmax, (double)l);
 #pragma unroll
         for (int q = 0; q < 4; ++q) a.lamw[q * a.plane + o] = lam[q];

@@ -3,18 +3,26 @@
 // (each face evaluated once), residual, forward-Euler update and the reduction
 // of the largest wave speed for the next step's dt, in one launch.
 //
-// Work decomposition.  The grid is cut into warp tasks: a strip of 30*V
-// output columns by TY rows.  Lane l of a warp holds V consecutive cells of a
-// row (one coalesced V-wide vector load per variable); lanes 0 and 31 hold the
-// strip's west and east neighbours (the "overlap" cells of Sec. 4.1.2) and
-// write nothing.  The warp marches up its rows keeping the current row, its
-// y-fluxes and the south face flux in registers, so every y-face is evaluated
-// once and shared by the two cells around it; x-faces are evaluated once by
-// the lane owning the cell east of the face, and passed to the lane on the
-// west with a shuffle.  No shared memory and no barrier is used in the march.
-// Ghost rows and columns at the physical boundary are produced by the row
-// loader from the boundary condition, which replaces copyOverlaps and the
-// ovlpE/N/W/S buffers.
+// Work decomposition.  The grid is cut into warp tasks: a strip of 30*V*K
+// output columns by TY rows.  Lane l of a warp holds V*K consecutive cells of
+// a row (V values of the arithmetic type A, each packing K cells; one
+// coalesced vector load per variable); lanes 0 and 31 hold the strip's west
+// and east neighbours (the "overlap" cells of Sec. 4.1.2) and write nothing.
+// The warp marches up its rows keeping the current row, its y-fluxes and the
+// south face flux in registers, so every y-face is evaluated once and shared
+// by the two cells around it; x-faces are evaluated once by the lane owning
+// the cell east of the face, and passed to the lane on the west with a
+// shuffle.  No barrier is used in the march.  Ghost rows and columns at the
+// physical boundary are produced by the row loader from the boundary
+// condition, which replaces copyOverlaps and the ovlpE/N/W/S buffers.
+//
+// Rows reach the registers in one of three ways (template parameter D):
+//   D = 0   register prefetch of the next row;
+//   D > 0   a D-deep ring of row segments in shared memory filled by TMA bulk
+//           copies (cp.async.bulk + mbarrier), one lane per warp issuing;
+//   D < 0   a -D-deep ring filled by each lane with cp.async for its own
+//           cells (no cross-lane synchronisation).
+// Strips touching the east or west boundary always use register prefetch.
 //
 // Ping-pong: step n reads buffer n % 2 and writes buffer (n + 1) % 2; n, dt
 // and lmax come from the device control block, so one graph of identical
@@ -25,9 +33,10 @@
 
 namespace fv {
 
-template <class R> struct StepArgs {
-  R *buf0;
-  R *buf1;
+// Launch arguments, in the storage type S of the state.
+template <class S> struct StepArgs {
+  S *buf0;
+  S *buf1;
   Ctrl *ctrl;
   int nx, ny;
   long long pitch;   // elements between rows
@@ -35,14 +44,14 @@ template <class R> struct StepArgs {
   int nstrips, nchunks, ntasks;
   double dx, dy;
   DtPolicy pol;
-  SysParams<R> sp;
+  SysParams<S> sp;
   int bc[4];
-  R bc_state[4][8];
+  S bc_state[4][8];
 };
 
-template <class R, int V> struct VecIO;
 // ld: read-only path (state never written during the launch); ldcg: L2-coherent
 // loads for the persistent batched kernel, whose launch also writes the state.
+template <class S, int N> struct VecIO;
 template <> struct VecIO<float, 1> {
   static __device__ __forceinline__ void ld(const float *p, float (&o)[1]) { o[0] = __ldg(p); }
   static __device__ __forceinline__ void ldcg(const float *p, float (&o)[1]) { o[0] = __ldcg(p); }
@@ -93,21 +102,21 @@ template <> struct VecIO<double, 2> {
   }
 };
 
-// Where a lane's V cells come from.  Interior strips (every lane's cells
-// inside [0, nx)) read V-wide vectors at column X; strips touching the east or
-// west boundary map each cell once per task: a real column, the ghost column
-// of the boundary condition, or (only for the idle halo lane of a ragged
-// strip) a clamped column whose values are never used.
-template <int V> struct LaneCols {
-  int col[V];
-  int dir[V];  // Dirichlet side of a ghost cell, -1 otherwise
+// Where a lane's N storage cells come from.  Interior strips (every lane's
+// cells inside [0, nx)) read N-wide vectors at column X; strips touching the
+// east or west boundary map each cell once per task: a real column, the ghost
+// column of the boundary condition, or (only for the idle halo lane of a
+// ragged strip) a clamped column whose values are never used.
+template <int N> struct LaneCols {
+  int col[N];
+  int dir[N];  // Dirichlet side of a ghost cell, -1 otherwise
 };
 
-template <int V, class R>
-static __device__ __forceinline__ LaneCols<V> lane_cols(const StepArgs<R> &a, int X) {
-  LaneCols<V> L;
+template <int N, class S>
+static __device__ __forceinline__ LaneCols<N> lane_cols(const StepArgs<S> &a, int X) {
+  LaneCols<N> L;
 #pragma unroll
-  for (int c = 0; c < V; ++c) {
+  for (int c = 0; c < N; ++c) {
     const int col = X + c;
     int sc = col, cs = -1;
     if (col < 0) {
@@ -125,8 +134,8 @@ static __device__ __forceinline__ LaneCols<V> lane_cols(const StepArgs<R> &a, in
 
 // Source row of row j (ghost rows -1 and ny from the boundary condition);
 // returns the Dirichlet side when the ghost row is a prescribed state.
-template <class R>
-static __device__ __forceinline__ int row_src(const StepArgs<R> &a, int j, int &dir) {
+template <class S>
+static __device__ __forceinline__ int row_src(const StepArgs<S> &a, int j, int &dir) {
   dir = -1;
   if (j < 0) {
     if (a.bc[kS] == kDirichlet) dir = kS;
@@ -139,40 +148,38 @@ static __device__ __forceinline__ int row_src(const StepArgs<R> &a, int j, int &
   return j;
 }
 
-template <int NV, int V, bool XIN, bool CG, class R>
-static __device__ __forceinline__ void load_row(const StepArgs<R> &a, const R *__restrict__ base,
-                                                const LaneCols<V> &L, int j, R (&W)[V][NV]) {
+// Load the lane's V values (V*K cells) of row j of every variable into W.
+template <int NV, int V, bool XIN, bool CG, class A>
+static __device__ __forceinline__ void load_row(const StepArgs<typename Ops<A>::S> &a,
+                                                const typename Ops<A>::S *__restrict__ base,
+                                                const LaneCols<V * Ops<A>::K> &L, int j, A (&W)[V][NV]) {
+  using S = typename Ops<A>::S;
+  constexpr int K = Ops<A>::K, N = V * K;
   int dir;
   const int sj = row_src(a, j, dir);
   if (dir >= 0) {
 #pragma unroll
     for (int c = 0; c < V; ++c)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[dir][v];
+      for (int v = 0; v < NV; ++v) W[c][v] = Ops<A>::splat(a.bc_state[dir][v]);
     return;
   }
-  const R *row = base + (long long)sj * a.pitch;
-  if (XIN) {
+  const S *row = base + (long long)sj * a.pitch;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      R t[V];
-      if (CG) VecIO<R, V>::ldcg(row + v * a.plane, t);
-      else VecIO<R, V>::ld(row + v * a.plane, t);
+  for (int v = 0; v < NV; ++v) {
+    S t[N];
+    if (XIN) {
+      if (CG) VecIO<S, N>::ldcg(row + v * a.plane, t);
+      else VecIO<S, N>::ld(row + v * a.plane, t);
+    } else {
 #pragma unroll
-      for (int c = 0; c < V; ++c) W[c][v] = t[c];
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < V; ++c) {
-      if (L.dir[c] >= 0) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[L.dir[c]][v];
-      } else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-          W[c][v] = CG ? __ldcg(row + v * a.plane + L.col[c]) : __ldg(row + v * a.plane + L.col[c]);
+      for (int c = 0; c < N; ++c) {
+        if (L.dir[c] >= 0) t[c] = a.bc_state[L.dir[c]][v];
+        else t[c] = CG ? __ldcg(row + v * a.plane + L.col[c]) : __ldg(row + v * a.plane + L.col[c]);
       }
     }
+#pragma unroll
+    for (int c = 0; c < V; ++c) W[c][v] = Ops<A>::pack(t + c * K);
   }
 }
 
@@ -180,121 +187,175 @@ static __device__ __forceinline__ void load_row(const StepArgs<R> &a, const R *_
 // the west-face flux of each cell (the first cell's west neighbour is the
 // previous lane's last cell), the east face from the next lane, and
 // dX = F~_{i+1/2} - F~_{i-1/2}.  Also returns the y-fluxes and y-speeds.
-template <class Sys, int V, class R>
-static __device__ __forceinline__ void row_x(const SysParams<R> &P, const R (&W)[V][Sys::NV],
-                                             R (&Fy)[V][Sys::NV], R (&sy)[V],
-                                             R (&dX)[V][Sys::NV]) {
+template <class Sys, int V, class A>
+static __device__ __forceinline__ void row_x(const SysParams<A> &P, const A (&W)[V][Sys::NV],
+                                             A (&Fy)[V][Sys::NV], A (&sy)[V], A (&dX)[V][Sys::NV]) {
   constexpr int NV = Sys::NV;
-  using O = Ops<R>;
-  R Fx[V][NV], sx[V];
+  using O = Ops<A>;
+  A Fx[V][NV], sx[V];
 #pragma unroll
   for (int c = 0; c < V; ++c) Sys::fluxes(W[c], P, Fx[c], sx[c], Fy[c], sy[c]);
-  R Fw[V][NV];
-  {
-    const R sL = __shfl_up_sync(0xffffffffu, sx[V - 1], 1);
-    const R hs = O::mul((R)0.5, O::max(sL, sx[0]));
+  A Fw[V][NV];
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    // values of the cells just west of this value's cells
+    const A sprev = c == 0 ? O::shfl_up(sx[V - 1], 1) : sx[c - 1];
+    const A sL = O::shift_in(sprev, sx[c]);
+    const A hs = O::mul(O::splat(0.5), O::max(sL, sx[c]));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const R WL = __shfl_up_sync(0xffffffffu, W[V - 1][v], 1);
-      const R FL = __shfl_up_sync(0xffffffffu, Fx[V - 1][v], 1);
-      Fw[0][v] = lf_face(WL, FL, W[0][v], Fx[0][v], hs);
+      const A wprev = c == 0 ? O::shfl_up(W[V - 1][v], 1) : W[c - 1][v];
+      const A fprev = c == 0 ? O::shfl_up(Fx[V - 1][v], 1) : Fx[c - 1][v];
+      Fw[c][v] = lf_face(O::shift_in(wprev, W[c][v]), O::shift_in(fprev, Fx[c][v]), W[c][v], Fx[c][v], hs);
     }
   }
 #pragma unroll
-  for (int c = 1; c < V; ++c) {
-    const R hs = O::mul((R)0.5, O::max(sx[c - 1], sx[c]));
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Fw[c][v] = lf_face(W[c - 1][v], Fx[c - 1][v], W[c][v], Fx[c][v], hs);
-  }
-#pragma unroll
   for (int v = 0; v < NV; ++v) {
+    const A first_next = O::shfl_down(Fw[0][v], 1);
 #pragma unroll
-    for (int c = 0; c + 1 < V; ++c) dX[c][v] = O::sub(Fw[c + 1][v], Fw[c][v]);
-    const R Fe = __shfl_down_sync(0xffffffffu, Fw[0][v], 1);
-    dX[V - 1][v] = O::sub(Fe, Fw[V - 1][v]);
+    for (int c = 0; c < V; ++c) {
+      const A next = c + 1 < V ? Fw[c + 1][v] : first_next;
+      dX[c][v] = O::sub(O::shift_out(Fw[c][v], next), Fw[c][v]);
+    }
   }
 }
 
 // Registers of one row of the march.
-template <class R, int V, int NV> struct RowState {
-  R W[V][NV];
-  R Fy[V][NV];
-  R sy[V];
-  R dX[V][NV];
+template <class A, int V, int NV> struct RowState {
+  A W[V][NV];
+  A Fy[V][NV];
+  A sy[V];
+  A dX[V][NV];
 };
 
 // Compute part of one row of the march (rows j and j+1 in registers): x-work
 // of row j+1, the y-face between rows j and j+1 evaluated once, update and
 // store of row j (by the writer lanes), and the new state's wave speed.
-template <class Sys, class R, int V, bool XIN, bool FIN>
-static __device__ __forceinline__ void advance_row(const StepArgs<R> &a, R *__restrict__ dst_lane, int X,
-                                                   int j, bool writer, R lx, R ly,
-                                                   RowState<R, V, Sys::NV> &cur,
-                                                   RowState<R, V, Sys::NV> &nxt, R (&Fs)[V][Sys::NV],
-                                                   R &lam_loc, bool &bad) {
-  constexpr int NV = Sys::NV;
-  using O = Ops<R>;
-  row_x<Sys, V>(a.sp, nxt.W, nxt.Fy, nxt.sy, nxt.dX);
-  R Wn[V][NV];
+template <class Sys, class A, int V, bool XIN, bool FIN>
+static __device__ __forceinline__ void advance_row(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+                                                   typename Ops<A>::S *__restrict__ dst_lane, int X, int j,
+                                                   bool writer, A lx, A ly, RowState<A, V, Sys::NV> &cur,
+                                                   RowState<A, V, Sys::NV> &nxt, A (&Fs)[V][Sys::NV],
+                                                   typename Ops<A>::S &lam_loc, unsigned &bad) {
+  using S = typename Ops<A>::S;
+  constexpr int NV = Sys::NV, K = Ops<A>::K, N = V * K;
+  using O = Ops<A>;
+  row_x<Sys, V>(P, nxt.W, nxt.Fy, nxt.sy, nxt.dX);
+  A Wn[V][NV];
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    const R hs = O::mul((R)0.5, O::max(cur.sy[c], nxt.sy[c]));
+    const A hs = O::mul(O::splat(0.5), O::max(cur.sy[c], nxt.sy[c]));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const R Fn = lf_face(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], hs);
+      const A Fn = lf_face(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], hs);
       Wn[c][v] = fv_update(cur.W[c][v], cur.dX[c][v], O::sub(Fn, Fs[c][v]), lx, ly);
       Fs[c][v] = Fn;
     }
   }
   if (writer) {
-    R *row = dst_lane + (long long)j * a.pitch;
-    if (XIN || X + V <= a.nx) {
+    S *row = dst_lane + (long long)j * a.pitch;
+    if (XIN || X + N <= a.nx) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        R t[V];
+        S t[N];
 #pragma unroll
-        for (int c = 0; c < V; ++c) t[c] = Wn[c][v];
-        VecIO<R, V>::st(row + v * a.plane, t);
+        for (int c = 0; c < V; ++c) O::unpack(Wn[c][v], t + c * K);
+        VecIO<S, N>::st(row + v * a.plane, t);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < V; ++c)
-        if (X + c < a.nx) {
+      for (int v = 0; v < NV; ++v) {
+        S t[N];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) __stcs(row + v * a.plane + c, Wn[c][v]);
-        }
+        for (int c = 0; c < V; ++c) O::unpack(Wn[c][v], t + c * K);
+#pragma unroll
+        for (int c = 0; c < N; ++c)
+          if (X + c < a.nx) __stcs(row + v * a.plane + c, t[c]);
+      }
     }
     if (FIN) {
 #pragma unroll
       for (int c = 0; c < V; ++c) {
-        if (XIN || X + c < a.nx) {
-          bool b;
-          const R l = Sys::lambda(Wn[c], a.sp, b);
-          lam_loc = O::max(lam_loc, l);
-          bad |= b;
+        // packed cells inside the grid (all of them on interior strips)
+        unsigned valid = (1u << K) - 1u;
+        if (!XIN) {
+          valid = 0u;
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (X + c * K + k < a.nx) valid |= 1u << k;
         }
+        unsigned b;
+        const A l = Sys::lambda(Wn[c], P, b);
+        lam_loc = fmax(lam_loc, O::hmax(l, valid));
+        bad |= b & valid;
       }
     }
   }
 }
 
 // One row of the march with register prefetch: `nxt` receives row j+1
-// (already prefetched in P) and P is refilled with row j+2.
-template <class Sys, class R, int V, bool XIN, bool FIN, bool CG>
-static __device__ __forceinline__ void march_row(const StepArgs<R> &a, const R *__restrict__ src,
-                                                 R *__restrict__ dst_lane, const LaneCols<V> &L,
-                                                 int X, int j, int y1, bool writer, R lx, R ly,
-                                                 RowState<R, V, Sys::NV> &cur,
-                                                 RowState<R, V, Sys::NV> &nxt,
-                                                 R (&P)[V][Sys::NV], R (&Fs)[V][Sys::NV],
-                                                 R &lam_loc, bool &bad) {
+// (already prefetched in Pf) and Pf is refilled with row j+2.
+template <class Sys, class A, int V, bool XIN, bool FIN, bool CG>
+static __device__ __forceinline__ void march_row(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+                                                 const typename Ops<A>::S *__restrict__ src,
+                                                 typename Ops<A>::S *__restrict__ dst_lane,
+                                                 const LaneCols<V * Ops<A>::K> &L, int X, int j, int y1,
+                                                 bool writer, A lx, A ly, RowState<A, V, Sys::NV> &cur,
+                                                 RowState<A, V, Sys::NV> &nxt, A (&Pf)[V][Sys::NV],
+                                                 A (&Fs)[V][Sys::NV], typename Ops<A>::S &lam_loc,
+                                                 unsigned &bad) {
   constexpr int NV = Sys::NV;
 #pragma unroll
   for (int c = 0; c < V; ++c)
 #pragma unroll
-    for (int v = 0; v < NV; ++v) nxt.W[c][v] = P[c][v];
-  if (j + 2 <= y1) load_row<NV, V, XIN, CG>(a, src, L, j + 2, P);
-  advance_row<Sys, R, V, XIN, FIN>(a, dst_lane, X, j, writer, lx, ly, cur, nxt, Fs, lam_loc, bad);
+    for (int v = 0; v < NV; ++v) nxt.W[c][v] = Pf[c][v];
+  if (j + 2 <= y1) load_row<NV, V, XIN, CG>(a, src, L, j + 2, Pf);
+  advance_row<Sys, A, V, XIN, FIN>(a, P, dst_lane, X, j, writer, lx, ly, cur, nxt, Fs, lam_loc, bad);
+}
+
+// March one warp task with register prefetch: rows [y0, y1) of the strip
+// whose lane l holds the V*K cells starting at column X.
+template <class Sys, class A, int V, bool XIN, bool FIN, bool CG = false>
+static __device__ __forceinline__ void march(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+                                             const typename Ops<A>::S *__restrict__ src,
+                                             typename Ops<A>::S *__restrict__ dst, int X, int y0, int y1,
+                                             bool writer, A lx, A ly, typename Ops<A>::S &lam_loc,
+                                             unsigned &bad) {
+  using S = typename Ops<A>::S;
+  constexpr int NV = Sys::NV, N = V * Ops<A>::K;
+  using O = Ops<A>;
+  LaneCols<N> L;
+  if (!XIN) L = lane_cols<N>(a, X);
+  const S *base = XIN ? src + X : src;
+  S *dst_lane = dst + X;
+  RowState<A, V, NV> RA, RB;
+  A Pf[V][NV], Fs[V][NV];
+  // row below the strip: only its y-fluxes are needed
+  load_row<NV, V, XIN, CG>(a, base, L, y0 - 1, RA.W);
+  load_row<NV, V, XIN, CG>(a, base, L, y0, RB.W);
+  if (y0 + 1 <= y1) load_row<NV, V, XIN, CG>(a, base, L, y0 + 1, Pf);
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    A Fx_[NV], sx_;
+    Sys::fluxes(RA.W[c], P, Fx_, sx_, RA.Fy[c], RA.sy[c]);
+  }
+  row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    const A hs = O::mul(O::splat(0.5), O::max(RA.sy[c], RB.sy[c]));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], hs);
+  }
+  // the two row states swap roles every row (unrolled by two: no copies)
+  int j = y0;
+  while (true) {
+    if (j >= y1) break;
+    march_row<Sys, A, V, XIN, FIN, CG>(a, P, base, dst_lane, L, X, j, y1, writer, lx, ly, RB, RA, Pf, Fs, lam_loc, bad);
+    ++j;
+    if (j >= y1) break;
+    march_row<Sys, A, V, XIN, FIN, CG>(a, P, base, dst_lane, L, X, j, y1, writer, lx, ly, RA, RB, Pf, Fs, lam_loc, bad);
+    ++j;
+  }
 }
 
 // ---------------------------------------------------------------- TMA rows
@@ -303,7 +364,7 @@ static __device__ __forceinline__ void march_row(const StepArgs<R> &a, const R *
 // warp owns a ring of D row slots, one mbarrier per slot; lane 0 issues, for
 // every variable, one bulk copy of the strip's row segment (widened to 16-byte
 // boundaries), so D rows per warp are in flight without spending registers.
-// A lane reads its V cells of a slot after the slot's barrier completes.
+// A lane reads its cells of a slot after the slot's barrier completes.
 // Every wait is bounded (%globaltimer); a wait that runs out marks the step
 // with a timeout error and the warp stops waiting (the step is then reported
 // as failed, never silently used).
@@ -344,26 +405,31 @@ static __device__ __forceinline__ unsigned long long timer_ns() {
   return t;
 }
 
-template <class R> struct TmaGeom {
-  static constexpr int kAlign = 16 / (int)sizeof(R);           // elements per 16 bytes
-  static constexpr __host__ __device__ int seg(int V) { return 32 * V + 2 * kAlign; }  // slot elements per variable
+template <class S> struct TmaGeom {
+  static constexpr int kAlign = 16 / (int)sizeof(S);  // elements per 16 bytes
+  static constexpr __host__ __device__ int seg(int N) { return 32 * N + 2 * kAlign; }  // slot elements per variable
 };
 
-template <class R, int V, int NV, int D> struct RowRing {
-  R *buf;                     // D slots x NV variables x SEG elements
+template <class A, int V, int NV, int D> struct RowRing {
+  using S = typename Ops<A>::S;
+  static constexpr int N = V * Ops<A>::K;
+  static constexpr int SEG = TmaGeom<S>::seg(N);
+  S *buf;                     // D slots x NV variables x SEG elements
   unsigned long long *bar;    // D barriers
   unsigned phase;             // bit k: parity the next wait on slot k expects
   int seg0;                   // first column of the staged segment (16-byte aligned)
   int lane_off;               // X - seg0
   unsigned bytes;             // bytes per variable per row
   bool broken;
-  static constexpr int SEG = TmaGeom<R>::seg(V);
 };
 
 // Lane 0 stages row j (relative row r of the task) into slot r % D.
-template <class R, int V, int NV, int D>
-static __device__ __forceinline__ void ring_issue(const StepArgs<R> &a, const R *__restrict__ src,
-                                                  RowRing<R, V, NV, D> &rg, int r, int j) {
+template <class A, int V, int NV, int D>
+static __device__ __forceinline__ void ring_issue(const StepArgs<typename Ops<A>::S> &a,
+                                                  const typename Ops<A>::S *__restrict__ src,
+                                                  RowRing<A, V, NV, D> &rg, int r, int j) {
+  using S = typename Ops<A>::S;
+  using RG = RowRing<A, V, NV, D>;
   int dir;
   const int sj = row_src(a, j, dir);
   if (dir >= 0 || rg.broken) return;  // a prescribed ghost row is not staged
@@ -372,19 +438,23 @@ static __device__ __forceinline__ void ring_issue(const StepArgs<R> &a, const R 
     unsigned long long *bar = rg.bar + slot;
     fence_proxy_async();
     mbar_arrive_expect_tx(bar, rg.bytes * NV);
-    const R *g = src + (long long)sj * a.pitch + rg.seg0;
-    R *sm = rg.buf + slot * NV * RowRing<R, V, NV, D>::SEG;
+    const S *g = src + (long long)sj * a.pitch + rg.seg0;
+    S *sm = rg.buf + slot * NV * RG::SEG;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) bulk_load(sm + v * RowRing<R, V, NV, D>::SEG, g + v * a.plane, rg.bytes, bar);
+    for (int v = 0; v < NV; ++v) bulk_load(sm + v * RG::SEG, g + v * a.plane, rg.bytes, bar);
   }
 }
 
-// Every lane takes its V cells of row j (relative row r) out of its slot,
+// Every lane takes its cells of row j (relative row r) out of its slot,
 // then the slot is refilled with relative row r + D (row j + D) if any.
-template <class R, int V, int NV, int D>
-static __device__ __forceinline__ void ring_fetch(const StepArgs<R> &a, const R *__restrict__ src,
-                                                  RowRing<R, V, NV, D> &rg, int r, int j, int nrows,
-                                                  R (&W)[V][NV]) {
+template <class A, int V, int NV, int D>
+static __device__ __forceinline__ void ring_fetch(const StepArgs<typename Ops<A>::S> &a,
+                                                  const typename Ops<A>::S *__restrict__ src,
+                                                  RowRing<A, V, NV, D> &rg, int r, int j, int nrows,
+                                                  A (&W)[V][NV]) {
+  using S = typename Ops<A>::S;
+  using RG = RowRing<A, V, NV, D>;
+  constexpr int K = Ops<A>::K;
   int dir;
   row_src(a, j, dir);
   const int slot = r % D;
@@ -392,7 +462,7 @@ static __device__ __forceinline__ void ring_fetch(const StepArgs<R> &a, const R 
 #pragma unroll
     for (int c = 0; c < V; ++c)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) W[c][v] = a.bc_state[dir][v];
+      for (int v = 0; v < NV; ++v) W[c][v] = Ops<A>::splat(a.bc_state[dir][v]);
   } else {
     if (!rg.broken) {
       const unsigned par = (rg.phase >> slot) & 1u;
@@ -410,68 +480,71 @@ static __device__ __forceinline__ void ring_fetch(const StepArgs<R> &a, const R 
       }
       rg.phase ^= 1u << slot;
     }
-    const R *sm = rg.buf + slot * NV * RowRing<R, V, NV, D>::SEG + rg.lane_off;
+    const S *sm = rg.buf + slot * NV * RG::SEG + rg.lane_off;
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int c = 0; c < V; ++c) W[c][v] = sm[v * RowRing<R, V, NV, D>::SEG + c];
+      for (int c = 0; c < V; ++c) W[c][v] = Ops<A>::pack(sm + v * RG::SEG + c * K);
   }
   __syncwarp();
-  if (r + D < nrows) ring_issue<R, V, NV, D>(a, src, rg, r + D, j + D);
+  if (r + D < nrows) ring_issue<A, V, NV, D>(a, src, rg, r + D, j + D);
 }
 
 // March one interior warp task through the TMA ring.
-template <class Sys, class R, int V, int D, bool FIN>
-static __device__ __forceinline__ void march_tma(const StepArgs<R> &a, const R *__restrict__ src,
-                                                 R *__restrict__ dst, RowRing<R, V, Sys::NV, D> &rg,
-                                                 int X, int y0, int y1, bool writer, R lx, R ly,
-                                                 R &lam_loc, bool &bad) {
-  constexpr int NV = Sys::NV;
-  using O = Ops<R>;
-  // the lanes' cells span [X_0, X_31 + V); stage that span widened to 16 bytes
+template <class Sys, class A, int V, int D, bool FIN>
+static __device__ __forceinline__ void march_tma(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+                                                 const typename Ops<A>::S *__restrict__ src,
+                                                 typename Ops<A>::S *__restrict__ dst,
+                                                 RowRing<A, V, Sys::NV, D> &rg, int X, int y0, int y1,
+                                                 bool writer, A lx, A ly, typename Ops<A>::S &lam_loc,
+                                                 unsigned &bad) {
+  using S = typename Ops<A>::S;
+  constexpr int NV = Sys::NV, N = V * Ops<A>::K;
+  using O = Ops<A>;
+  // the lanes' cells span [X_0, X_31 + N); stage that span widened to 16 bytes
   const int x_first = __shfl_sync(0xffffffffu, X, 0);
-  const int x_end = x_first + 32 * V;
-  constexpr int AL = TmaGeom<R>::kAlign;
+  const int x_end = x_first + 32 * N;
+  constexpr int AL = TmaGeom<S>::kAlign;
   rg.seg0 = x_first / AL * AL;
   const int seg1 = (x_end + AL - 1) / AL * AL;
-  rg.bytes = (unsigned)((seg1 - rg.seg0) * (int)sizeof(R));
+  rg.bytes = (unsigned)((seg1 - rg.seg0) * (int)sizeof(S));
   rg.lane_off = X - rg.seg0;
-  R *dst_lane = dst + X;
+  S *dst_lane = dst + X;
   const int nrows = y1 - y0 + 2;  // rows y0 - 1 .. y1
   const int pre = nrows < D ? nrows : D;
-  for (int r = 0; r < pre; ++r) ring_issue<R, V, NV, D>(a, src, rg, r, y0 - 1 + r);
-  RowState<R, V, NV> A, B;
-  R Fs[V][NV];
-  ring_fetch<R, V, NV, D>(a, src, rg, 0, y0 - 1, nrows, A.W);
+  for (int r = 0; r < pre; ++r) ring_issue<A, V, NV, D>(a, src, rg, r, y0 - 1 + r);
+  RowState<A, V, NV> RA, RB;
+  A Fs[V][NV];
+  ring_fetch<A, V, NV, D>(a, src, rg, 0, y0 - 1, nrows, RA.W);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    R Fx_[NV], sx_;
-    Sys::fluxes(A.W[c], a.sp, Fx_, sx_, A.Fy[c], A.sy[c]);
+    A Fx_[NV], sx_;
+    Sys::fluxes(RA.W[c], P, Fx_, sx_, RA.Fy[c], RA.sy[c]);
   }
-  ring_fetch<R, V, NV, D>(a, src, rg, 1, y0, nrows, B.W);
-  row_x<Sys, V>(a.sp, B.W, B.Fy, B.sy, B.dX);
+  ring_fetch<A, V, NV, D>(a, src, rg, 1, y0, nrows, RB.W);
+  row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    const R hs = O::mul((R)0.5, O::max(A.sy[c], B.sy[c]));
+    const A hs = O::mul(O::splat(0.5), O::max(RA.sy[c], RB.sy[c]));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(A.W[c][v], A.Fy[c][v], B.W[c][v], B.Fy[c][v], hs);
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], hs);
   }
   int j = y0;
   while (true) {
     if (j >= y1) break;
-    ring_fetch<R, V, NV, D>(a, src, rg, j - y0 + 2, j + 1, nrows, A.W);
-    advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, B, A, Fs, lam_loc, bad);
+    ring_fetch<A, V, NV, D>(a, src, rg, j - y0 + 2, j + 1, nrows, RA.W);
+    advance_row<Sys, A, V, true, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad);
     ++j;
     if (j >= y1) break;
-    ring_fetch<R, V, NV, D>(a, src, rg, j - y0 + 2, j + 1, nrows, B.W);
-    advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, A, B, Fs, lam_loc, bad);
+    ring_fetch<A, V, NV, D>(a, src, rg, j - y0 + 2, j + 1, nrows, RB.W);
+    advance_row<Sys, A, V, true, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad);
     ++j;
   }
 }
 
 // ---------------------------------------------------------------- cp.async rows
-// Second staging scheme for interior strips: every lane copies its own V
-// cells of a row into its own slot of a per-warp ring in shared memory with
+// Second staging scheme for interior strips: every lane copies its own cells
+// of a row into its own slot of a per-warp ring in shared memory with
 // cp.async (each lane later reads only what it copied, so no cross-lane
 // synchronisation is needed); D - 1 rows stay in flight per lane.
 
@@ -485,40 +558,40 @@ static __device__ __forceinline__ void cp_async_bytes16(void *sdst, const void *
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
 }
 static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
+template <int W>
 static __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+  asm volatile("cp.async.wait_group %0;" ::"n"(W) : "memory");
 }
 
-template <class R, int V>
-static __device__ __forceinline__ void cp_async_cells(R *sdst, const R *gsrc) {
-  constexpr int B = V * (int)sizeof(R);
+template <class S, int N>
+static __device__ __forceinline__ void cp_async_cells(S *sdst, const S *gsrc) {
+  constexpr int B = N * (int)sizeof(S);
   if (B == 4) cp_async_bytes4(sdst, gsrc);
   else if (B == 8) cp_async_bytes8(sdst, gsrc);
   else if (B == 16) cp_async_bytes16(sdst, gsrc);
   else {
 #pragma unroll
-    for (int c = 0; c < V; ++c) {
-      if (sizeof(R) == 8) cp_async_bytes8(sdst + c, gsrc + c);
+    for (int c = 0; c < N; ++c) {
+      if (sizeof(S) == 8) cp_async_bytes8(sdst + c, gsrc + c);
       else cp_async_bytes4(sdst + c, gsrc + c);
     }
   }
 }
 
-template <class R, int V, int NV, int D> struct LaneRing {
-  R *buf;  // this lane's D slots x NV variables x V cells, lane-interleaved
+// A lane's private ring: D slots x NV variables x N cells, lanes interleaved
+// so a warp's copies of one variable land in one contiguous 32 * N span.
+template <class S, int N, int NV, int D> struct LaneRing {
+  S *buf;
+  __device__ __forceinline__ S *slot(int s, int v) const { return buf + ((s * NV + v) * 32) * N; }
 };
 
-// Lane-private slot address of (slot, variable): lanes are interleaved so a
-// warp's copies of one variable land in one contiguous 32 * V span.
-template <class R, int V, int NV, int D>
-static __device__ __forceinline__ R *lane_slot(const LaneRing<R, V, NV, D> &rg, int slot, int v) {
-  return rg.buf + ((slot * NV + v) * 32) * V;
-}
-
-template <class R, int V, int NV, int D>
-static __device__ __forceinline__ void lring_issue(const StepArgs<R> &a, const R *__restrict__ src_lane,
-                                                   const LaneRing<R, V, NV, D> &rg, int r, int j) {
+template <class A, int V, int NV, int D>
+static __device__ __forceinline__ void lring_issue(const StepArgs<typename Ops<A>::S> &a,
+                                                   const typename Ops<A>::S *__restrict__ src_lane,
+                                                   const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
+                                                   int r, int j) {
+  using S = typename Ops<A>::S;
+  constexpr int N = V * Ops<A>::K;
   int dir;
   const int sj = row_src(a, j, dir);
   const int slot = r % D;
@@ -526,26 +599,25 @@ static __device__ __forceinline__ void lring_issue(const StepArgs<R> &a, const R
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int c = 0; c < V; ++c) lane_slot(rg, slot, v)[c] = a.bc_state[dir][v];
+      for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = a.bc_state[dir][v];
   } else {
-    const R *g = src_lane + (long long)sj * a.pitch;
+    const S *g = src_lane + (long long)sj * a.pitch;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) cp_async_cells<R, V>(lane_slot(rg, slot, v), g + v * a.plane);
+    for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), g + v * a.plane);
   }
   cp_async_commit();
 }
 
-template <class R, int V, int NV, int D>
-static __device__ __forceinline__ void lring_read(const LaneRing<R, V, NV, D> &rg, int r, R (&W)[V][NV]) {
+template <class A, int V, int NV, int D>
+static __device__ __forceinline__ void lring_read(const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
+                                                  int r, A (&W)[V][NV]) {
+  constexpr int K = Ops<A>::K;
   const int slot = r % D;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    R t[V];
-    const R *p = lane_slot(rg, slot, v);
+    const typename Ops<A>::S *p = rg.slot(slot, v);
 #pragma unroll
-    for (int c = 0; c < V; ++c) t[c] = p[c];
-#pragma unroll
-    for (int c = 0; c < V; ++c) W[c][v] = t[c];
+    for (int c = 0; c < V; ++c) W[c][v] = Ops<A>::pack(p + c * K);
   }
 }
 
@@ -554,43 +626,46 @@ static __device__ __forceinline__ void lring_read(const LaneRing<R, V, NV, D> &r
 // lane has issued rows up to r + D - 2 and waits until at most D - 2 copy
 // groups are pending, i.e. row r has landed.  A slot is refilled only after
 // the row read from it has been consumed by the flux computation.
-template <class Sys, class R, int V, int D, bool FIN>
-static __device__ __forceinline__ void march_async(const StepArgs<R> &a, const R *__restrict__ src,
-                                                   R *__restrict__ dst, const LaneRing<R, V, Sys::NV, D> &rg,
-                                                   int X, int y0, int y1, bool writer, R lx, R ly,
-                                                   R &lam_loc, bool &bad) {
+template <class Sys, class A, int V, int D, bool FIN>
+static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+                                                   const typename Ops<A>::S *__restrict__ src,
+                                                   typename Ops<A>::S *__restrict__ dst,
+                                                   const LaneRing<typename Ops<A>::S, V * Ops<A>::K, Sys::NV, D> &rg,
+                                                   int X, int y0, int y1, bool writer, A lx, A ly,
+                                                   typename Ops<A>::S &lam_loc, unsigned &bad) {
+  using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV;
-  using O = Ops<R>;
-  const R *src_lane = src + X;
-  R *dst_lane = dst + X;
+  using O = Ops<A>;
+  const S *src_lane = src + X;
+  S *dst_lane = dst + X;
   const int nrows = y1 - y0 + 2;
   // prologue: rows 0 .. D-2 in flight (empty groups past the end keep the count)
 #pragma unroll
   for (int r = 0; r < D - 1; ++r) {
-    if (r < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, r, y0 - 1 + r);
+    if (r < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, r, y0 - 1 + r);
     else cp_async_commit();
   }
-  RowState<R, V, NV> A, B;
-  R Fs[V][NV];
+  RowState<A, V, NV> RA, RB;
+  A Fs[V][NV];
   cp_async_wait<D - 2>();
-  lring_read<R, V, NV, D>(rg, 0, A.W);
+  lring_read<A, V, NV, D>(rg, 0, RA.W);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    R Fx_[NV], sx_;
-    Sys::fluxes(A.W[c], a.sp, Fx_, sx_, A.Fy[c], A.sy[c]);
+    A Fx_[NV], sx_;
+    Sys::fluxes(RA.W[c], P, Fx_, sx_, RA.Fy[c], RA.sy[c]);
   }
-  if (D - 1 < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, D - 1, y0 - 1 + D - 1);
+  if (D - 1 < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, D - 1, y0 - 1 + D - 1);
   else cp_async_commit();
   cp_async_wait<D - 2>();
-  lring_read<R, V, NV, D>(rg, 1, B.W);
-  row_x<Sys, V>(a.sp, B.W, B.Fy, B.sy, B.dX);
-  if (D < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, D, y0 - 1 + D);
+  lring_read<A, V, NV, D>(rg, 1, RB.W);
+  row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
+  if (D < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, D, y0 - 1 + D);
   else cp_async_commit();
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    const R hs = O::mul((R)0.5, O::max(A.sy[c], B.sy[c]));
+    const A hs = O::mul(O::splat(0.5), O::max(RA.sy[c], RB.sy[c]));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(A.W[c][v], A.Fy[c][v], B.W[c][v], B.Fy[c][v], hs);
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], hs);
   }
   int j = y0;
   while (true) {
@@ -598,9 +673,9 @@ static __device__ __forceinline__ void march_async(const StepArgs<R> &a, const R
     {
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
-      lring_read<R, V, NV, D>(rg, r, A.W);
-      advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, B, A, Fs, lam_loc, bad);
-      if (r + D - 1 < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
+      lring_read<A, V, NV, D>(rg, r, RA.W);
+      advance_row<Sys, A, V, true, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad);
+      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -608,9 +683,9 @@ static __device__ __forceinline__ void march_async(const StepArgs<R> &a, const R
     {
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
-      lring_read<R, V, NV, D>(rg, r, B.W);
-      advance_row<Sys, R, V, true, FIN>(a, dst_lane, X, j, writer, lx, ly, A, B, Fs, lam_loc, bad);
-      if (r + D - 1 < nrows) lring_issue<R, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
+      lring_read<A, V, NV, D>(rg, r, RB.W);
+      advance_row<Sys, A, V, true, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad);
+      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -618,124 +693,83 @@ static __device__ __forceinline__ void march_async(const StepArgs<R> &a, const R
   cp_async_wait<0>();
 }
 
-template <class R, int V, int NV, int D>
-constexpr __host__ __device__ int async_smem_bytes(int NW) {
-  return NW * D * NV * 32 * V * (int)sizeof(R);
-}
-
-// Dynamic shared memory of a block of the TMA variant.
-template <class R, int V, int NV, int D>
+// Dynamic shared memory per block of the staging rings.
+template <class A, int V, int NV, int D>
 constexpr __host__ __device__ int tma_smem_bytes(int NW) {
-  return NW * (D * NV * TmaGeom<R>::seg(V) * (int)sizeof(R) + D * 8);
+  using S = typename Ops<A>::S;
+  return NW * (D * NV * TmaGeom<S>::seg(V * Ops<A>::K) * (int)sizeof(S) + D * 8);
+}
+template <class A, int V, int NV, int D>
+constexpr __host__ __device__ int async_smem_bytes(int NW) {
+  return NW * D * NV * 32 * V * Ops<A>::K * (int)sizeof(typename Ops<A>::S);
 }
 
-// March one warp task: rows [y0, y1) of the strip whose lane l holds the V
-// cells starting at column X.
-template <class Sys, class R, int V, bool XIN, bool FIN, bool CG = false>
-static __device__ __forceinline__ void march(const StepArgs<R> &a, const R *__restrict__ src,
-                                             R *__restrict__ dst, int X, int y0, int y1, bool writer,
-                                             R lx, R ly, R &lam_loc, bool &bad) {
-  constexpr int NV = Sys::NV;
-  using O = Ops<R>;
-  LaneCols<V> L;
-  if (!XIN) L = lane_cols<V>(a, X);
-  const R *base = XIN ? src + X : src;
-  R *dst_lane = dst + X;
-  RowState<R, V, NV> A, B;
-  R P[V][NV], Fs[V][NV];
-  // row below the strip: only its y-fluxes are needed
-  load_row<NV, V, XIN, CG>(a, base, L, y0 - 1, A.W);
-  load_row<NV, V, XIN, CG>(a, base, L, y0, B.W);
-  if (y0 + 1 <= y1) load_row<NV, V, XIN, CG>(a, base, L, y0 + 1, P);
-#pragma unroll
-  for (int c = 0; c < V; ++c) {
-    R Fx_[NV], sx_;
-    Sys::fluxes(A.W[c], a.sp, Fx_, sx_, A.Fy[c], A.sy[c]);
-  }
-  row_x<Sys, V>(a.sp, B.W, B.Fy, B.sy, B.dX);
-#pragma unroll
-  for (int c = 0; c < V; ++c) {
-    const R hs = O::mul((R)0.5, O::max(A.sy[c], B.sy[c]));
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(A.W[c][v], A.Fy[c][v], B.W[c][v], B.Fy[c][v], hs);
-  }
-  // the two row states swap roles every row (unrolled by two: no copies)
-  int j = y0;
-  while (true) {
-    if (j >= y1) break;
-    march_row<Sys, R, V, XIN, FIN, CG>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, B, A, P, Fs, lam_loc, bad);
-    ++j;
-    if (j >= y1) break;
-    march_row<Sys, R, V, XIN, FIN, CG>(a, base, dst_lane, L, X, j, y1, writer, lx, ly, A, B, P, Fs, lam_loc, bad);
-    ++j;
-  }
-}
-
+// The fused step.  A: arithmetic type (float, double or F2 = two packed FP32
+// cells); V: values of A per lane; TY: rows per warp task; NW: warps per block;
 // FIN: this launch also reduces lmax(W^{n+1}) and closes the step (every
-// system but spray, whose source kernel closes the step instead).
-// D > 0: interior strips stage rows through a D-deep TMA ring in shared
-// memory (dynamic shared memory of tma_smem_bytes<R, V, NV, D>(NW) bytes).
-// D < 0: interior strips stage rows through a per-lane cp.async ring of
-// depth -D (dynamic shared memory of async_smem_bytes<R, V, NV, -D>(NW)).
-template <class Sys, class R, int V, int TY, int NW, bool FIN = true, int MINB = 1, int D = 0>
+// system but spray, whose source kernel closes the step instead); MINB: blocks
+// per SM the register budget targets; D: row staging (see the file header).
+template <class Sys, class A, int V, int TY, int NW, bool FIN = true, int MINB = 1, int D = 0>
 __global__ void __launch_bounds__(NW * 32, MINB)
-fv_step_kernel(const StepArgs<R> a) {
-  constexpr int NV = Sys::NV;
+fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
+  using S = typename Ops<A>::S;
+  constexpr int NV = Sys::NV, N = V * Ops<A>::K;
   __shared__ double s_lam[NW];
   __shared__ int s_bad[NW];
   __shared__ StepStart s_st;
   extern __shared__ __align__(128) unsigned char s_dyn[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  constexpr int DD = D > 0 ? D : 1;
+  constexpr int DT = D > 0 ? D : 1;
   constexpr int DA = D < 0 ? -D : 2;
-  RowRing<R, V, NV, DD> rg;
-  LaneRing<R, V, NV, DA> lrg;
-  if (D < 0) lrg.buf = reinterpret_cast<R *>(s_dyn) + warp * (DA * NV * 32 * V) + lane * V;
+  RowRing<A, V, NV, DT> rg;
+  LaneRing<S, N, NV, DA> lrg;
   if (D > 0) {
-    constexpr int slot_bytes = DD * NV * TmaGeom<R>::seg(V) * (int)sizeof(R);
-    unsigned char *mine = s_dyn + warp * (slot_bytes + DD * 8);
-    rg.buf = reinterpret_cast<R *>(mine);
+    constexpr int slot_bytes = DT * NV * RowRing<A, V, NV, DT>::SEG * (int)sizeof(S);
+    unsigned char *mine = s_dyn + warp * (slot_bytes + DT * 8);
+    rg.buf = reinterpret_cast<S *>(mine);
     rg.bar = reinterpret_cast<unsigned long long *>(mine + slot_bytes);
     rg.phase = 0u;
     rg.broken = false;
     if (lane == 0)
-      for (int k = 0; k < DD; ++k) mbar_init(rg.bar + k, 1);
+      for (int k = 0; k < DT; ++k) mbar_init(rg.bar + k, 1);
     fence_proxy_async();
     __syncwarp();
   }
+  if (D < 0) lrg.buf = reinterpret_cast<S *>(s_dyn) + warp * (DA * NV * 32 * N) + lane * N;
   if (threadIdx.x == 0) s_st = read_step_start(a.pol, a.ctrl);
   __syncthreads();
   const StepStart st = s_st;
-  R lam_loc = (R)0;
-  bool bad = false;
+  S lam_loc = (S)0;
+  unsigned bad = 0u;
 
   if (st.run) {
     const long long n = st.step;
-    const R *__restrict__ src = (n & 1) ? a.buf1 : a.buf0;
-    R *__restrict__ dst = (n & 1) ? a.buf0 : a.buf1;
-    const R lx = (R)(st.dt / a.dx);
-    const R ly = (R)(st.dt / a.dy);
+    const S *__restrict__ src = (n & 1) ? a.buf1 : a.buf0;
+    S *__restrict__ dst = (n & 1) ? a.buf0 : a.buf1;
+    const SysParams<A> P = splat_params<A>(a.sp);
+    const A lx = Ops<A>::splat((S)(st.dt / a.dx));
+    const A ly = Ops<A>::splat((S)(st.dt / a.dy));
     const bool writer = lane >= 1 && lane <= 30;
     const int gw = blockIdx.x * NW + warp;
     const int GW = gridDim.x * NW;
     for (int task = gw; task < a.ntasks; task += GW) {
       const int sx_ = task % a.nstrips;
       const int cy = task / a.nstrips;
-      const int X = sx_ * (30 * V) + (lane - 1) * V;
+      const int X = sx_ * (30 * N) + (lane - 1) * N;
       const int y0 = cy * TY;
       const int y1 = min(y0 + TY, a.ny);
       // warp-uniform: does every lane of the strip read real columns only?
-      const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
-      if (D > 0 && xin) march_tma<Sys, R, V, DD, FIN>(a, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (D < 0 && xin) march_async<Sys, R, V, DA, FIN>(a, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (xin) march<Sys, R, V, true, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else march<Sys, R, V, false, FIN>(a, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
+      if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (D < 0 && xin) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (xin) march<Sys, A, V, true, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else march<Sys, A, V, false, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }
   }
 
   if (!FIN) return;
-  finish_step<NW>(a.ctrl, st, (double)lam_loc, bad, s_lam, s_bad);
+  finish_step<NW>(a.ctrl, st, (double)lam_loc, bad != 0u, s_lam, s_bad);
 }
 
 }  // namespace fv

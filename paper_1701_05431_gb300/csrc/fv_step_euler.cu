@@ -1,34 +1,36 @@
 // fv_step_euler.cu -- fused step kernels of the Euler system (Sec. 5,
-// Eq. (Euler)), one per tile candidate: cells per lane V, rows per warp task
-// TY, warps per block NW, the blocks per SM the register budget targets, and
-// the depth D of the TMA row ring (0: register prefetch).
+// Eq. (Euler)), one per tile candidate: arithmetic type (FP64, FP32, or F2 =
+// two FP32 cells per packed FP32x2 instruction), values per lane V, rows per
+// warp task TY, warps per block NW, the blocks per SM the register budget
+// targets, and the row staging D (0 register prefetch, > 0 TMA ring,
+// < 0 cp.async ring).
 #include "fv_internal.h"
 #include "fv_step.cuh"
 
 namespace fv {
 
-#define FV_VARIANT(R, PREC, V, TY, NW, MB, D, DESC)                                                   \
+#define FV_VARIANT(A, PREC, V, TY, NW, MB, D, DESC)                                                   \
   out.push_back(Variant{kEuler, PREC, V, TY, NW, MB, D,                                                 \
-                        (D) > 0 ? tma_smem_bytes<R, V, 4, (D > 0 ? D : 1)>(NW)                          \
-                                : (D) < 0 ? async_smem_bytes<R, V, 4, (D < 0 ? -D : 1)>(NW) : 0,         \
-                        reinterpret_cast<const void *>(&fv_step_kernel<Euler, R, V, TY, NW, true, MB, D>), DESC})
+                        (D) > 0 ? tma_smem_bytes<A, V, 4, (D > 0 ? D : 1)>(NW)                          \
+                                : (D) < 0 ? async_smem_bytes<A, V, 4, (D < 0 ? -D : 1)>(NW) : 0,         \
+                        reinterpret_cast<const void *>(&fv_step_kernel<Euler, A, V, TY, NW, true, MB, D>), DESC})
 
 void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT(double, 0, 1, 64, 4, 1, 0, "euler f64 v1 ty64 w4");
   FV_VARIANT(double, 0, 1, 32, 4, 1, 0, "euler f64 v1 ty32 w4");
   FV_VARIANT(double, 0, 1, 64, 4, 4, -4, "euler f64 v1 ty64 w4 b4 async4");
+  FV_VARIANT(F2, 1, 1, 64, 4, 5, -6, "euler f32 x2 v1 ty64 w4 b5 async6");
+  FV_VARIANT(F2, 1, 1, 64, 4, 4, -6, "euler f32 x2 v1 ty64 w4 b4 async6");
+  FV_VARIANT(F2, 1, 1, 64, 4, 6, -6, "euler f32 x2 v1 ty64 w4 b6 async6");
+  FV_VARIANT(F2, 1, 1, 64, 4, 5, -8, "euler f32 x2 v1 ty64 w4 b5 async8");
+  FV_VARIANT(F2, 1, 2, 64, 4, 3, -4, "euler f32 x2 v2 ty64 w4 b3 async4");
   FV_VARIANT(float, 1, 2, 64, 4, 5, -6, "euler f32 v2 ty64 w4 b5 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 5, -4, "euler f32 v2 ty64 w4 b5 async4");
   FV_VARIANT(float, 1, 2, 64, 4, 5, -8, "euler f32 v2 ty64 w4 b5 async8");
-  FV_VARIANT(float, 1, 2, 64, 4, 4, -6, "euler f32 v2 ty64 w4 b4 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 4, -8, "euler f32 v2 ty64 w4 b4 async8");
-  FV_VARIANT(float, 1, 2, 128, 4, 5, -6, "euler f32 v2 ty128 w4 b5 async6");
-  FV_VARIANT(float, 1, 2, 32, 4, 5, -6, "euler f32 v2 ty32 w4 b5 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 0, "euler f32 v2 ty64 w4 b5");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 4, "euler f32 v2 ty64 w4 b5 tma4");
-  FV_VARIANT(float, 1, 2, 64, 4, 4, 6, "euler f32 v2 ty64 w4 b4 tma6");
   FV_VARIANT(float, 1, 1, 64, 4, 8, 0, "euler f32 v1 ty64 w4 b8");
-  FV_VARIANT(float, 1, 1, 64, 4, 8, -6, "euler f32 v1 ty64 w4 b8 async6");
 }
 
 }  // namespace fv
