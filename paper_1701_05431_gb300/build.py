@@ -20,6 +20,12 @@ LIB = os.path.join(OUT_DIR, "libfv.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# Translation units whose kernels use packed FP32x2 arithmetic: every FP
+# operation there is an explicit add/sub/mul/fma, and without this flag ptxas
+# fuses a packed multiply and a following packed add into one packed FMA even
+# when both carry an explicit rounding modifier, which would round
+# differently from the scalar kernels.
+PER_FILE_FLAGS = {"fv_step_euler.cu": ["--fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -54,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *PER_FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
