@@ -20,12 +20,8 @@ LIB = os.path.join(OUT_DIR, "libfv.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-# Translation units whose kernels use packed FP32x2 arithmetic: every FP
-# operation there is an explicit add/sub/mul/fma, and without this flag ptxas
-# fuses a packed multiply and a following packed add into one packed FMA even
-# when both carry an explicit rounding modifier, which would round
-# differently from the scalar kernels.
-PER_FILE_FLAGS = {"fv_step_euler.cu": ["--fmad=false"]}
+# Extra flags for individual translation units (none needed at present).
+PER_FILE_FLAGS: dict = {}
 
 
 def _nvcc() -> str:
