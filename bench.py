@@ -111,6 +111,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device: str = "cpu") -> float:
+    """Largest value over all ranks (the slowest rank's time); identity on one
+    process.  device: where the reduction tensor lives ("cuda:k" for NCCL,
+    "cpu" for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(cells: int, steps_per_job: int, jobs: int, world_size: int, max_ms: float) -> float:
+    """Cell-updates/s of the whole job: every rank advances its own replica of
+    `cells` cells by jobs * steps_per_job steps, timed by the slowest rank."""
+    return cells * steps_per_job * jobs * world_size / (max_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -317,11 +336,7 @@ def main():
         ev1.record(stream)
         barrier()
         ck_res = ck.stop() if ck else None
-        ms = ev0.elapsed_time(ev1)
-        if ws > 1:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), f"cuda:{local}")
         info = s.kernel_info()[1]
         s.close()
         return ms, ck_res, info
@@ -336,7 +351,7 @@ def main():
     # ---- FP32-bulk headline
     ms32, clk, kinfo32 = time_jobs("f32", args.steps, args.warmup, clocks=(rank == 0))
     launches = args.steps * nsteps_job
-    value32 = ncell * nsteps_job * args.steps * ws / (ms32 / 1e3)
+    value32 = whole_job_throughput(ncell, nsteps_job, args.steps, ws, ms32)
     hbm, peak_kind = peaks()
     algo_bytes_32 = 2 * nvar * 4 * ncell          # one read + one write per cell
     avg_launch_s = ms32 / 1e3 / launches
@@ -364,7 +379,7 @@ def main():
     if not args.no_fp64:
         k64 = max(1, min(args.steps, 2))
         ms64, _, kinfo64 = time_jobs("f64", k64, 1)
-        value64 = ncell * nsteps_job * k64 * ws / (ms64 / 1e3)
+        value64 = whole_job_throughput(ncell, nsteps_job, k64, ws, ms64)
         algo64 = 2 * nvar * 8 * ncell
         avg64 = ms64 / 1e3 / (k64 * nsteps_job)
         out["fp64"] = {"value": value64, "unit": "cell-updates/s", "ms_per_step": ms64 / k64,
