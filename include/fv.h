@@ -175,6 +175,24 @@ fv_status fv_kernel_candidate(int system, int precision, int index, const char *
  * library on the host.  1 <= Q <= 128. */
 fv_status fv_gauss_legendre(int Q, double *x, double *w);
 
+/* No-allocation totals.  The paper has no counterpart: this entry point is
+ * for callers that must not let the library allocate device memory (work
+ * enqueued while their stream is captured into a CUDA graph, loops that
+ * forbid allocator calls, frameworks that own all device memory).  Same
+ * per-variable totals sum_ij W_v * cell_area as fv_totals, for a caller-owned
+ * device state of nvar x ny x nx values of dtype (FV_F64 or FV_F32, layout
+ * above), written as nvar doubles to the caller's device buffer `totals`,
+ * queued on `stream` without synchronising.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine: its partial sums use a fixed 128 KiB array
+ * in the library's device image (per GPU, kept until the process exits), so
+ * nvar is limited to 8 (FV_ERR_INVALID_ARG otherwise, with the reason in
+ * fv_last_error(NULL)).  The first call on a device looks up that array's
+ * device address with the device current; make that first call before any
+ * stream capture.  All calls on a device share the array: calls that overlap
+ * on the GPU race and must be ordered by the caller. */
+fv_status fv_totals_noalloc(const void *state, int dtype, int nvar, int nx, int ny, double cell_area,
+                            double *totals, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched instances.  Many independent problems of the same system and
  * precision (advection or Euler; sizes, boundary conditions, parameters and

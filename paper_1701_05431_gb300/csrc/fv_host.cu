@@ -76,6 +76,10 @@ struct fv_ctx {
 
 static std::string g_init_error;
 
+namespace fv {
+void set_global_error(const std::string &msg) { g_init_error = msg; }
+}  // namespace fv
+
 static fv_status fail(fv_ctx *c, fv_status s, const std::string &msg) {
   if (c) c->err = msg;
   else g_init_error = msg;

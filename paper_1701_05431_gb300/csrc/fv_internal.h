@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
 #include <vector>
 
 #include "fv_device.cuh"
@@ -44,6 +45,9 @@ cudaError_t launch_totals(int prec, int nvar, const void *state, int nx, int ny,
                           long long plane, double *partials, int nblocks, double *out,
                           double cell_area, cudaStream_t s);
 int totals_blocks(int ny);
+
+// Record the message fv_last_error(NULL) returns (fv_host.cu).
+void set_global_error(const std::string &msg);
 
 // Spray source step (fv_spray.cu).
 struct SourceLaunch {

@@ -96,6 +96,9 @@ def load(build_if_missing: bool = True):
     for name in EXPORTS:
         if name not in ("fv_status_string", "fv_last_error", "fv_destroy"):
             getattr(L, name).restype = ctypes.c_int
+    L.fv_totals_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, vp, vp]
+    L.fv_totals_noalloc.restype = ctypes.c_int
     _declare_batch(L)
     _lib = L
     return L
@@ -268,6 +271,16 @@ class Solver:
         d = ctypes.c_char_p()
         _check(self.lib.fv_kernel_info(self.ctx, ctypes.byref(v), ctypes.byref(d)), self.ctx, self.lib)
         return v.value, d.value.decode()
+
+
+def totals_noalloc(state, totals, cell_area: float, stream: int = 0) -> int:
+    """fv_totals_noalloc on a device state tensor (nvar, ny, nx) into a device
+    tensor of nvar float64 values; returns the status."""
+    L = load()
+    nvar, ny, nx = state.shape
+    p, dev = _ptr(state)
+    q, _ = _ptr(totals)
+    return L.fv_totals_noalloc(p, _dtype_code(state), int(nvar), int(nx), int(ny), float(cell_area), q, stream)
 
 
 def kernel_candidates(system: str, precision: str):
