@@ -19,18 +19,15 @@ void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT(double, 0, 1, 64, 4, 1, 0, "euler f64 v1 ty64 w4");
   FV_VARIANT(double, 0, 1, 32, 4, 1, 0, "euler f64 v1 ty32 w4");
   FV_VARIANT(double, 0, 1, 64, 4, 4, -4, "euler f64 v1 ty64 w4 b4 async4");
-  FV_VARIANT(F2, 1, 1, 64, 4, 5, -6, "euler f32 x2 v1 ty64 w4 b5 async6");
-  FV_VARIANT(F2, 1, 1, 64, 4, 4, -6, "euler f32 x2 v1 ty64 w4 b4 async6");
-  FV_VARIANT(F2, 1, 1, 64, 4, 6, -6, "euler f32 x2 v1 ty64 w4 b6 async6");
-  FV_VARIANT(F2, 1, 1, 64, 4, 5, -8, "euler f32 x2 v1 ty64 w4 b5 async8");
-  FV_VARIANT(F2, 1, 2, 64, 4, 3, -4, "euler f32 x2 v2 ty64 w4 b3 async4");
   FV_VARIANT(float, 1, 2, 64, 4, 5, -6, "euler f32 v2 ty64 w4 b5 async6");
+  FV_VARIANT(float, 1, 2, 64, 4, 4, -6, "euler f32 v2 ty64 w4 b4 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 5, -4, "euler f32 v2 ty64 w4 b5 async4");
-  FV_VARIANT(float, 1, 2, 64, 4, 5, -8, "euler f32 v2 ty64 w4 b5 async8");
   FV_VARIANT(float, 1, 2, 64, 4, 4, -8, "euler f32 v2 ty64 w4 b4 async8");
+  FV_VARIANT(float, 1, 2, 32, 4, 5, -6, "euler f32 v2 ty32 w4 b5 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 0, "euler f32 v2 ty64 w4 b5");
   FV_VARIANT(float, 1, 2, 64, 4, 5, 4, "euler f32 v2 ty64 w4 b5 tma4");
   FV_VARIANT(float, 1, 1, 64, 4, 8, 0, "euler f32 v1 ty64 w4 b8");
+  FV_VARIANT(F2, 1, 1, 64, 4, 4, -6, "euler f32 x2 v1 ty64 w4 b4 async6");
 }
 
 }  // namespace fv
