@@ -389,6 +389,18 @@ def main():
         out["fp32_speedup_vs_fp64"] = value32 / value64
         out["fp64"]["gpu_launches"] = k64 * nsteps_job
 
+    # ---- bfloat16 storage (FP32 arithmetic), 16 B per cell-update
+    if not args.no_fp64:
+        kb = max(1, min(args.steps, 3))
+        msb, _, kinfob = time_jobs("bf16", kb, 2)
+        valueb = whole_job_throughput(ncell, nsteps_job, kb, ws, msb)
+        algob = 2 * nvar * 2 * ncell
+        avgb = msb / 1e3 / (kb * nsteps_job)
+        out["bf16_storage"] = {"value": valueb, "unit": "cell-updates/s", "ms_per_step": msb / kb, "steps": kb,
+                               "kernel": kinfob, "hbm_gbs_achieved": algob / avgb / 1e9,
+                               "hbm_frac": algob / avgb / 1e9 / hbm,
+                               "note": "bfloat16 state, FP32 arithmetic, FP64 dt/t/totals; accuracy below"}
+
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
         s = fvlib.Solver(d, "f32", stream=sptr, tune=args.tune)
@@ -424,7 +436,7 @@ def main():
     if os.path.exists(golden):
         g = np.load(golden)
         acc = {}
-        for precision in ("f32", "f64"):
+        for precision in ("f32", "f64", "bf16"):
             s = fvlib.Solver(d, precision, stream=sptr)
             s.set_state(prim_dev, primitive=True)
             s.run(int(g["steps"]))

@@ -47,10 +47,13 @@ enum { FV_ADVECTION = 0 /* (1) */, FV_EULER = 1 /* (4) */, FV_SPRAY = 2 /* (6) *
 
 /* Storage and arithmetic precision of the state.
  *   FV_F64: FP64 storage and FP64 arithmetic;
- *   FV_F32: FP32 storage and FP32 flux/update arithmetic.
+ *   FV_F32: FP32 storage and FP32 flux/update arithmetic;
+ *   FV_BF16: bfloat16 storage (rounded to nearest even after every step)
+ *     with FP32 arithmetic; advection and Euler only, single instances only.
  * In every precision dt, t and the conservation totals are FP64, and the
- * spray source's maximum-entropy solve is FP64. */
-enum { FV_F64 = 0, FV_F32 = 1 };
+ * spray source's maximum-entropy solve is FP64.  fv_set_state and
+ * fv_get_state exchange FP64 or FP32 arrays in every precision. */
+enum { FV_F64 = 0, FV_F32 = 1, FV_BF16 = 2 };
 
 /* Boundary conditions, per side (Sec. 4.2, copyOverlaps):
  *   periodic: the wrapped neighbour cell (E must pair with W, N with S);

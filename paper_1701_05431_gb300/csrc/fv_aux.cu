@@ -14,6 +14,12 @@ namespace fv {
 template <class S>
 static __device__ __forceinline__ double rd(const S *p, long long k) { return (double)p[k]; }
 
+// Narrowing of a double to a storage type (round to nearest even).
+template <class R> static __device__ __forceinline__ R from_double(double x) { return (R)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x) {
+  return __double2bfloat16(x);
+}
+
 // One thread per cell.  src is contiguous nvar x ny x nx; state is pitched.
 // Primitive -> conserved, in FP64 and in the same operation order as the
 // definition: rho E = p/(gamma - 1) + rho (u u + v v)/2; momenta = rho u, rho v
@@ -28,7 +34,7 @@ __global__ void load_state_kernel(int system, const S *__restrict__ src, int pri
     const int j = (int)(k / nx), i = (int)(k % nx);
     const long long o = (long long)j * pitch + i;
     if (system == kAdvection) {
-      state[o] = (R)rd(src, k);
+      state[o] = from_double<R>(rd(src, k));
     } else if (system == kEuler) {
       double w0 = rd(src, k), w1 = rd(src, ncell + k), w2 = rd(src, 2 * ncell + k),
              w3 = rd(src, 3 * ncell + k);
@@ -39,10 +45,10 @@ __global__ void load_state_kernel(int system, const S *__restrict__ src, int pri
         const double q = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
         w3 = __dadd_rn(__ddiv_rn(p, __dsub_rn(gamma, 1.0)), __ddiv_rn(__dmul_rn(rho, q), 2.0));
       }
-      state[o] = (R)w0;
-      state[plane + o] = (R)w1;
-      state[2 * plane + o] = (R)w2;
-      state[3 * plane + o] = (R)w3;
+      state[o] = from_double<R>(w0);
+      state[plane + o] = from_double<R>(w1);
+      state[2 * plane + o] = from_double<R>(w2);
+      state[3 * plane + o] = from_double<R>(w3);
     } else {
       double w[6];
 #pragma unroll
@@ -52,7 +58,7 @@ __global__ void load_state_kernel(int system, const S *__restrict__ src, int pri
         w[5] = __dmul_rn(w[2], w[5]);
       }
 #pragma unroll
-      for (int v = 0; v < 6; ++v) state[v * plane + o] = (R)w[v];
+      for (int v = 0; v < 6; ++v) state[v * plane + o] = from_double<R>(w[v]);
     }
   }
 }
@@ -76,13 +82,20 @@ cudaError_t launch_load_state(int system, int prec, const void *src, int src_f32
     else
       load_state_kernel<double, double><<<g, th, 0, s>>>(system, (const double *)src, primitive,
                                                          (double *)state, nx, ny, pitch, plane, gamma);
-  } else {
+  } else if (prec == 1) {
     if (src_f32)
       load_state_kernel<float, float><<<g, th, 0, s>>>(system, (const float *)src, primitive,
                                                        (float *)state, nx, ny, pitch, plane, gamma);
     else
       load_state_kernel<double, float><<<g, th, 0, s>>>(system, (const double *)src, primitive,
                                                         (float *)state, nx, ny, pitch, plane, gamma);
+  } else {
+    if (src_f32)
+      load_state_kernel<float, __nv_bfloat16><<<g, th, 0, s>>>(system, (const float *)src, primitive,
+                                                               (__nv_bfloat16 *)state, nx, ny, pitch, plane, gamma);
+    else
+      load_state_kernel<double, __nv_bfloat16><<<g, th, 0, s>>>(system, (const double *)src, primitive,
+                                                                (__nv_bfloat16 *)state, nx, ny, pitch, plane, gamma);
   }
   return cudaGetLastError();
 }
@@ -96,7 +109,7 @@ __global__ void store_state_kernel(int nvar, const R *__restrict__ state, D *__r
        k += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(k / nx), i = (int)(k % nx);
     const long long o = (long long)j * pitch + i;
-    for (int v = 0; v < nvar; ++v) dst[v * ncell + k] = (D)state[v * plane + o];
+    for (int v = 0; v < nvar; ++v) dst[v * ncell + k] = (D)to_double(state[v * plane + o]);
   }
 }
 
@@ -111,13 +124,20 @@ cudaError_t launch_store_state(int prec, int nvar, const void *state, void *dst,
     else
       store_state_kernel<double, double><<<g, th, 0, s>>>(nvar, (const double *)state, (double *)dst,
                                                           nx, ny, pitch, plane);
-  } else {
+  } else if (prec == 1) {
     if (dst_f32)
       store_state_kernel<float, float><<<g, th, 0, s>>>(nvar, (const float *)state, (float *)dst, nx,
                                                         ny, pitch, plane);
     else
       store_state_kernel<float, double><<<g, th, 0, s>>>(nvar, (const float *)state, (double *)dst, nx,
                                                          ny, pitch, plane);
+  } else {
+    if (dst_f32)
+      store_state_kernel<__nv_bfloat16, float><<<g, th, 0, s>>>(nvar, (const __nv_bfloat16 *)state, (float *)dst,
+                                                                nx, ny, pitch, plane);
+    else
+      store_state_kernel<__nv_bfloat16, double><<<g, th, 0, s>>>(nvar, (const __nv_bfloat16 *)state,
+                                                                 (double *)dst, nx, ny, pitch, plane);
   }
   return cudaGetLastError();
 }
@@ -125,10 +145,11 @@ cudaError_t launch_store_state(int prec, int nvar, const void *state, void *dst,
 // ------------------------------------------------------------------ seed lmax
 // lmax(W^0) and admissibility of a freshly loaded state, with the same
 // per-cell function the step kernel applies to every new state.
-template <class Sys, class R>
-__global__ void seed_lambda_kernel(const R *__restrict__ state, int nx, int ny, long long pitch,
-                                   long long plane, SysParams<R> P, Ctrl *ctrl, int slot) {
+template <class Sys, class A>
+__global__ void seed_lambda_kernel(const typename Ops<A>::S *__restrict__ state, int nx, int ny, long long pitch,
+                                   long long plane, SysParams<typename Ops<A>::P> Pp, Ctrl *ctrl, int slot) {
   constexpr int NV = Sys::NV;
+  const SysParams<A> P = splat_params<A>(Pp);
   const long long ncell = (long long)nx * ny;
   double l = 0.0;
   bool bad = false;
@@ -136,13 +157,13 @@ __global__ void seed_lambda_kernel(const R *__restrict__ state, int nx, int ny, 
        k += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(k / nx), i = (int)(k % nx);
     const long long o = (long long)j * pitch + i;
-    R W[NV];
+    A W[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) W[v] = state[v * plane + o];
+    for (int v = 0; v < NV; ++v) W[v] = Ops<A>::pack(state + v * plane + o);
     unsigned b;
-    R lc = Sys::lambda(W, P, b);
+    const A lc = Sys::lambda(W, P, b);
     bad |= b != 0u;
-    l = fmax(l, (double)lc);
+    l = fmax(l, (double)Ops<A>::hmax(lc, 1u));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
@@ -164,12 +185,18 @@ cudaError_t launch_seed_lambda(int system, int prec, const void *state, int nx, 
     if (system == kAdvection) seed_lambda_kernel<Advection, double><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
     else if (system == kEuler) seed_lambda_kernel<Euler, double><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
     else seed_lambda_kernel<Spray, double><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
-  } else {
+  } else if (prec == 1) {
     SysParams<float> P{(float)p0, (float)p1};
     const float *st = (const float *)state;
     if (system == kAdvection) seed_lambda_kernel<Advection, float><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
     else if (system == kEuler) seed_lambda_kernel<Euler, float><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
     else seed_lambda_kernel<Spray, float><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+  } else {
+    SysParams<float> P{(float)p0, (float)p1};
+    const __nv_bfloat16 *st = (const __nv_bfloat16 *)state;
+    if (system == kAdvection) seed_lambda_kernel<Advection, BF><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+    else if (system == kEuler) seed_lambda_kernel<Euler, BF><<<g, th, 0, s>>>(st, nx, ny, pitch, plane, P, ctrl, slot);
+    else return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -206,7 +233,7 @@ __global__ void totals_partial_kernel(int nvar, const R *__restrict__ state, int
     Neu acc{0.0, 0.0};
     for (int j = blockIdx.x; j < ny; j += gridDim.x) {
       const R *row = state + v * plane + (long long)j * pitch;
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) neu_add(acc, (double)row[i]);
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) neu_add(acc, to_double(row[i]));
     }
     sh[threadIdx.x] = acc;
     __syncthreads();
@@ -240,9 +267,12 @@ cudaError_t launch_totals(int prec, int nvar, const void *state, int nx, int ny,
   if (prec == 0)
     totals_partial_kernel<double><<<nblocks, kTotThreads, 0, s>>>(nvar, (const double *)state, nx, ny,
                                                                   pitch, plane, partials);
-  else
+  else if (prec == 1)
     totals_partial_kernel<float><<<nblocks, kTotThreads, 0, s>>>(nvar, (const float *)state, nx, ny,
                                                                  pitch, plane, partials);
+  else
+    totals_partial_kernel<__nv_bfloat16><<<nblocks, kTotThreads, 0, s>>>(nvar, (const __nv_bfloat16 *)state, nx,
+                                                                         ny, pitch, plane, partials);
   totals_final_kernel<<<1, 32, 0, s>>>(nvar, partials, nblocks, out, cell_area);
   return cudaGetLastError();
 }

@@ -10,6 +10,7 @@
 // bit, and any tile shape gives the same bits.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,7 +41,8 @@ struct Ctrl {
 template <class R> struct Ops;
 
 // Every arithmetic type A used by the kernels provides:
-//   S        storage type of one cell value (float or double)
+//   S        storage type of one cell value (float, double or bfloat16)
+//   P        type of parameters, boundary states and wave-speed maxima
 //   K        cells packed in one A (1, or 2 for F2)
 //   add/sub/mul/fma/rcp/sqrt/abs/max/neg   per component, explicitly rounded
 //   splat(s), pack(p), unpack(x, p)        conversions to and from storage
@@ -55,6 +57,7 @@ template <class R> struct Ops;
 
 template <> struct Ops<double> {
   using S = double;
+  using P = double;
   static constexpr int K = 1;
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
@@ -79,6 +82,7 @@ template <> struct Ops<double> {
 
 template <> struct Ops<float> {
   using S = float;
+  using P = float;
   static constexpr int K = 1;
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
@@ -122,6 +126,7 @@ struct __align__(8) F2 {
 
 template <> struct Ops<F2> {
   using S = float;
+  using P = float;
   static constexpr int K = 2;
   static __device__ __forceinline__ unsigned long long b(F2 a) {
     unsigned long long r;
@@ -183,13 +188,56 @@ template <> struct Ops<F2> {
   }
 };
 
+// One cell held in FP32 for arithmetic and stored as bfloat16 (16 bytes per
+// Euler cell-update instead of 32): loads widen bfloat16 to FP32 exactly,
+// stores round to nearest even.  All arithmetic is the FP32 arithmetic of
+// Ops<float>.
+struct BF {
+  float v;
+};
+
+template <> struct Ops<BF> {
+  using S = __nv_bfloat16;
+  using P = float;
+  static constexpr int K = 1;
+  using F = Ops<float>;
+  static __device__ __forceinline__ BF add(BF a, BF b) { return BF{F::add(a.v, b.v)}; }
+  static __device__ __forceinline__ BF sub(BF a, BF b) { return BF{F::sub(a.v, b.v)}; }
+  static __device__ __forceinline__ BF mul(BF a, BF b) { return BF{F::mul(a.v, b.v)}; }
+  static __device__ __forceinline__ BF fma(BF a, BF b, BF c) { return BF{F::fma(a.v, b.v, c.v)}; }
+  static __device__ __forceinline__ BF rcp(BF a) { return BF{F::rcp(a.v)}; }
+  static __device__ __forceinline__ BF sqrt(BF a) { return BF{F::sqrt(a.v)}; }
+  static __device__ __forceinline__ BF abs(BF a) { return BF{fabsf(a.v)}; }
+  static __device__ __forceinline__ BF max(BF a, BF b) { return BF{fmaxf(a.v, b.v)}; }
+  static __device__ __forceinline__ BF neg(BF a) { return BF{-a.v}; }
+  static __device__ __forceinline__ BF splat(float s) { return BF{s}; }
+  static __device__ __forceinline__ BF pack(const __nv_bfloat16 *p) { return BF{__bfloat162float(p[0])}; }
+  static __device__ __forceinline__ void unpack(BF a, __nv_bfloat16 *p) { p[0] = __float2bfloat16_rn(a.v); }
+  static __device__ __forceinline__ BF shfl_up(BF a, int d) { return BF{__shfl_up_sync(0xffffffffu, a.v, d)}; }
+  static __device__ __forceinline__ BF shfl_down(BF a, int d) { return BF{__shfl_down_sync(0xffffffffu, a.v, d)}; }
+  static __device__ __forceinline__ BF shift_in(BF prev, BF) { return prev; }
+  static __device__ __forceinline__ BF shift_out(BF, BF next) { return next; }
+  static __device__ __forceinline__ unsigned not_pos(BF a) { return (a.v > 0.0f) ? 0u : 1u; }
+  static __device__ __forceinline__ unsigned not_fin(BF a) { return (fabsf(a.v) <= 3.0e38f) ? 0u : 1u; }
+  static __device__ __forceinline__ float hmax(BF a, unsigned mask) { return (mask & 1u) ? a.v : 0.0f; }
+};
+
+// Widening of a stored value to double (totals, conversions).
+static __device__ __forceinline__ double to_double(double x) { return x; }
+static __device__ __forceinline__ double to_double(float x) { return (double)x; }
+static __device__ __forceinline__ double to_double(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
+// Parameter type of a storage type.
+template <class S> struct ParamOf { using T = S; };
+template <> struct ParamOf<__nv_bfloat16> { using T = float; };
+
 // Parameters of the system, in the arithmetic precision.
 template <class R> struct SysParams {
   R p0, p1;   // advection: a_x, a_y | Euler: gamma, gamma - 1 | spray: unused
 };
 
 template <class A>
-static __device__ __forceinline__ SysParams<A> splat_params(const SysParams<typename Ops<A>::S> &p) {
+static __device__ __forceinline__ SysParams<A> splat_params(const SysParams<typename Ops<A>::P> &p) {
   return SysParams<A>{Ops<A>::splat(p.p0), Ops<A>::splat(p.p1)};
 }
 

@@ -118,8 +118,10 @@ extern "C" const char *fv_last_error(const fv_ctx *ctx) {
 static fv_status validate(const fv_config *c) {
   if (!c) return fail(nullptr, FV_ERR_INVALID_ARG, "config is NULL");
   if (nvar_of(c->system) == 0) return fail(nullptr, FV_ERR_INVALID_ARG, "unknown system");
-  if (c->precision != FV_F64 && c->precision != FV_F32)
+  if (c->precision != FV_F64 && c->precision != FV_F32 && c->precision != FV_BF16)
     return fail(nullptr, FV_ERR_INVALID_ARG, "unknown precision");
+  if (c->precision == FV_BF16 && c->system == FV_SPRAY)
+    return fail(nullptr, FV_ERR_INVALID_ARG, "bf16 storage is not available for the spray system");
   if (c->nx < 1 || c->ny < 1) return fail(nullptr, FV_ERR_INVALID_ARG, "nx and ny must be >= 1");
   if ((long long)c->nx * c->ny > (1LL << 34))
     return fail(nullptr, FV_ERR_INVALID_ARG, "grid too large");
@@ -209,16 +211,17 @@ static StepArgs<R> make_args(const fv_ctx *c, const Variant &V) {
   a.pol.fixed_dt = c->cfg.fixed_dt;
   a.pol.dt_cap = 1.0e308;
   if (c->cfg.system == FV_SPRAY && c->cfg.params[1] > 0.0) a.pol.dt_cap = 0.5 * c->cfg.params[1];
+  using PT = typename ParamOf<R>::T;
   if (c->cfg.system == FV_ADVECTION) {
-    a.sp.p0 = (R)c->cfg.params[0];
-    a.sp.p1 = (R)c->cfg.params[1];
+    a.sp.p0 = (PT)c->cfg.params[0];
+    a.sp.p1 = (PT)c->cfg.params[1];
   } else if (c->cfg.system == FV_EULER) {
-    a.sp.p0 = (R)c->cfg.params[0];
-    a.sp.p1 = (R)(c->cfg.params[0] - 1.0);
+    a.sp.p0 = (PT)c->cfg.params[0];
+    a.sp.p1 = (PT)(c->cfg.params[0] - 1.0);
   }
   for (int s = 0; s < 4; ++s) {
     a.bc[s] = c->cfg.bc[s];
-    for (int v = 0; v < 8; ++v) a.bc_state[s][v] = (R)c->cfg.bc_state[s][v];
+    for (int v = 0; v < 8; ++v) a.bc_state[s][v] = (PT)c->cfg.bc_state[s][v];
   }
   return a;
 }
@@ -233,8 +236,13 @@ static fv_status launch_step(fv_ctx *c, cudaStream_t s) {
     pol = a.pol;
     void *args[] = {&a};
     e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
-  } else {
+  } else if (V.precision == 1) {
     StepArgs<float> a = make_args<float>(c, V);
+    pol = a.pol;
+    void *args[] = {&a};
+    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
+  } else {
+    StepArgs<__nv_bfloat16> a = make_args<__nv_bfloat16>(c, V);
     pol = a.pol;
     void *args[] = {&a};
     e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
@@ -318,7 +326,7 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
   fv_ctx *c = new fv_ctx();
   c->cfg = *cfg;
   c->nvar = nvar_of(cfg->system);
-  c->esize = cfg->precision == FV_F64 ? 8 : 4;
+  c->esize = cfg->precision == FV_F64 ? 8 : cfg->precision == FV_F32 ? 4 : 2;
   // pitch: a multiple of 32 elements (128 B in FP32, 256 B in FP64) so every
   // row and every V-wide vector access is aligned
   c->pitch = ((long long)cfg->nx + 31) / 32 * 32;
@@ -372,7 +380,7 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     if ((e = cudaMalloc(&c->lamw, sizeof(double) * 4 * c->plane)) != cudaSuccess) return bail(e, "cudaMalloc(lamw)");
     c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, c->sms);
   }
-  int prec = cfg->precision == FV_F64 ? 0 : 1;
+  int prec = cfg->precision;  // 0 f64, 1 f32, 2 bf16 storage
   int vi = default_variant(cfg->system, prec);
   if (cfg->tune >= 2) {
     auto cand = candidates(cfg->system, prec);
@@ -440,7 +448,7 @@ static fv_status seed(fv_ctx *c, long long step, double t) {
     FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 4 * c->plane, c->stream));
   double p0 = c->cfg.params[0], p1 = c->cfg.params[1];
   if (c->cfg.system == FV_EULER) p1 = c->cfg.params[0] - 1.0;
-  FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision == FV_F64 ? 0 : 1, c->buf[step & 1],
+  FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision, c->buf[step & 1],
                                 c->cfg.nx, c->cfg.ny, c->pitch, c->plane, p0, p1, c->ctrl,
                                 (int)(step % 3), c->stream));
   fv_status st = read_ctrl(c);
@@ -473,7 +481,7 @@ extern "C" fv_status fv_set_state(fv_ctx *c, const void *src, int src_is_device,
     FV_CUDA(c, cudaMemcpyAsync(c->staging, src, sbytes, cudaMemcpyHostToDevice, c->stream));
     dsrc = c->staging;
   }
-  const int prec = c->cfg.precision == FV_F64 ? 0 : 1;
+  const int prec = c->cfg.precision;
   FV_CUDA(c, launch_load_state(c->cfg.system, prec, dsrc, src_dtype == FV_F32, layout == FV_PRIMITIVE,
                                c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->cfg.params[0],
                                c->stream));
@@ -488,9 +496,9 @@ extern "C" fv_status fv_get_state(fv_ctx *c, void *dst, int dst_is_device, int d
   fv_status st = read_ctrl(c);
   if (st != FV_OK) return st;
   const void *cur = c->buf[c->h_ctrl->step & 1];
-  const int prec = c->cfg.precision == FV_F64 ? 0 : 1;
+  const int prec = c->cfg.precision;
   const size_t dsz = dst_dtype == FV_F64 ? 8 : 4;
-  const bool same = (dst_dtype == FV_F64) == (prec == 0);
+  const bool same = (dst_dtype == FV_F64 && prec == 0) || (dst_dtype == FV_F32 && prec == 1);
   const long long ncell = (long long)c->cfg.nx * c->cfg.ny;
   if (same) {
     // planes are contiguous at stride ny * pitch: one 2D copy of nvar * ny rows
@@ -609,7 +617,7 @@ extern "C" fv_status fv_totals(fv_ctx *c, double *totals) {
   fv_status st = read_ctrl(c);
   if (st != FV_OK) return st;
   const int nb = totals_blocks(c->cfg.ny);
-  FV_CUDA(c, launch_totals(c->cfg.precision == FV_F64 ? 0 : 1, c->nvar, c->buf[c->h_ctrl->step & 1],
+  FV_CUDA(c, launch_totals(c->cfg.precision, c->nvar, c->buf[c->h_ctrl->step & 1],
                            c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->partials, nb, c->d_totals,
                            c->dx * c->dy, c->stream));
   FV_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_totals, sizeof(double) * c->nvar, cudaMemcpyDeviceToHost,
@@ -704,8 +712,8 @@ extern "C" fv_status fv_gauss_legendre(int Q, double *x, double *w) {
 }
 
 extern "C" fv_status fv_kernel_candidate(int system, int precision, int index, const char **desc) {
-  if (!desc || (precision != FV_F64 && precision != FV_F32)) return FV_ERR_INVALID_ARG;
-  auto cand = candidates(system, precision == FV_F64 ? 0 : 1);
+  if (!desc || (precision != FV_F64 && precision != FV_F32 && precision != FV_BF16)) return FV_ERR_INVALID_ARG;
+  auto cand = candidates(system, precision);
   if (index < 0 || index >= (int)cand.size()) return FV_ERR_INVALID_ARG;
   *desc = all_variants()[cand[index]].desc;
   return FV_OK;

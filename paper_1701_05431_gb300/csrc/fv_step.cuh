@@ -44,9 +44,9 @@ template <class S> struct StepArgs {
   int nstrips, nchunks, ntasks;
   double dx, dy;
   DtPolicy pol;
-  SysParams<S> sp;
+  SysParams<typename ParamOf<S>::T> sp;
   int bc[4];
-  S bc_state[4][8];
+  typename ParamOf<S>::T bc_state[4][8];
 };
 
 // ld: read-only path (state never written during the launch); ldcg: L2-coherent
@@ -99,6 +99,44 @@ template <> struct VecIO<double, 2> {
   }
   static __device__ __forceinline__ void st(double *p, const double (&o)[2]) {
     __stcs(reinterpret_cast<double2 *>(p), make_double2(o[0], o[1]));
+  }
+};
+
+template <> struct VecIO<__nv_bfloat16, 2> {
+  static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, __nv_bfloat16 (&o)[2]) {
+    const __nv_bfloat162 t = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
+    o[0] = t.x; o[1] = t.y;
+  }
+  static __device__ __forceinline__ void ldcg(const __nv_bfloat16 *p, __nv_bfloat16 (&o)[2]) {
+    const __nv_bfloat162 t = __ldcg(reinterpret_cast<const __nv_bfloat162 *>(p));
+    o[0] = t.x; o[1] = t.y;
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, const __nv_bfloat16 (&o)[2]) {
+    __nv_bfloat162 t;
+    t.x = o[0]; t.y = o[1];
+    __stcs(reinterpret_cast<__nv_bfloat162 *>(p), t);
+  }
+};
+template <> struct VecIO<__nv_bfloat16, 4> {
+  static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, __nv_bfloat16 (&o)[4]) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&t.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&t.y);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  static __device__ __forceinline__ void ldcg(const __nv_bfloat16 *p, __nv_bfloat16 (&o)[4]) {
+    const uint2 t = __ldcg(reinterpret_cast<const uint2 *>(p));
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&t.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&t.y);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, const __nv_bfloat16 (&o)[4]) {
+    __nv_bfloat162 a, b;
+    a.x = o[0]; a.y = o[1]; b.x = o[2]; b.y = o[3];
+    uint2 t;
+    t.x = *reinterpret_cast<const unsigned *>(&a);
+    t.y = *reinterpret_cast<const unsigned *>(&b);
+    __stcs(reinterpret_cast<uint2 *>(p), t);
   }
 };
 
@@ -174,7 +212,7 @@ static __device__ __forceinline__ void load_row(const StepArgs<typename Ops<A>::
     } else {
 #pragma unroll
       for (int c = 0; c < N; ++c) {
-        if (L.dir[c] >= 0) t[c] = a.bc_state[L.dir[c]][v];
+        if (L.dir[c] >= 0) t[c] = (S)a.bc_state[L.dir[c]][v];
         else t[c] = CG ? __ldcg(row + v * a.plane + L.col[c]) : __ldg(row + v * a.plane + L.col[c]);
       }
     }
@@ -236,7 +274,7 @@ static __device__ __forceinline__ void advance_row(const StepArgs<typename Ops<A
                                                    typename Ops<A>::S *__restrict__ dst_lane, int X, int j,
                                                    bool writer, A lx, A ly, RowState<A, V, Sys::NV> &cur,
                                                    RowState<A, V, Sys::NV> &nxt, A (&Fs)[V][Sys::NV],
-                                                   typename Ops<A>::S &lam_loc, unsigned &bad) {
+                                                   typename Ops<A>::P &lam_loc, unsigned &bad) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV, K = Ops<A>::K, N = V * K;
   using O = Ops<A>;
@@ -302,7 +340,7 @@ static __device__ __forceinline__ void march_row(const StepArgs<typename Ops<A>:
                                                  const LaneCols<V * Ops<A>::K> &L, int X, int j, int y1,
                                                  bool writer, A lx, A ly, RowState<A, V, Sys::NV> &cur,
                                                  RowState<A, V, Sys::NV> &nxt, A (&Pf)[V][Sys::NV],
-                                                 A (&Fs)[V][Sys::NV], typename Ops<A>::S &lam_loc,
+                                                 A (&Fs)[V][Sys::NV], typename Ops<A>::P &lam_loc,
                                                  unsigned &bad) {
   constexpr int NV = Sys::NV;
 #pragma unroll
@@ -319,7 +357,7 @@ template <class Sys, class A, int V, bool XIN, bool FIN, bool CG = false>
 static __device__ __forceinline__ void march(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
                                              const typename Ops<A>::S *__restrict__ src,
                                              typename Ops<A>::S *__restrict__ dst, int X, int y0, int y1,
-                                             bool writer, A lx, A ly, typename Ops<A>::S &lam_loc,
+                                             bool writer, A lx, A ly, typename Ops<A>::P &lam_loc,
                                              unsigned &bad) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV, N = V * Ops<A>::K;
@@ -496,7 +534,7 @@ static __device__ __forceinline__ void march_tma(const StepArgs<typename Ops<A>:
                                                  const typename Ops<A>::S *__restrict__ src,
                                                  typename Ops<A>::S *__restrict__ dst,
                                                  RowRing<A, V, Sys::NV, D> &rg, int X, int y0, int y1,
-                                                 bool writer, A lx, A ly, typename Ops<A>::S &lam_loc,
+                                                 bool writer, A lx, A ly, typename Ops<A>::P &lam_loc,
                                                  unsigned &bad) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV, N = V * Ops<A>::K;
@@ -599,7 +637,7 @@ static __device__ __forceinline__ void lring_issue(const StepArgs<typename Ops<A
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = a.bc_state[dir][v];
+      for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = (S)a.bc_state[dir][v];
   } else {
     const S *g = src_lane + (long long)sj * a.pitch;
 #pragma unroll
@@ -632,7 +670,7 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
                                                    typename Ops<A>::S *__restrict__ dst,
                                                    const LaneRing<typename Ops<A>::S, V * Ops<A>::K, Sys::NV, D> &rg,
                                                    int X, int y0, int y1, bool writer, A lx, A ly,
-                                                   typename Ops<A>::S &lam_loc, unsigned &bad) {
+                                                   typename Ops<A>::P &lam_loc, unsigned &bad) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV;
   using O = Ops<A>;
@@ -740,7 +778,7 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
   if (threadIdx.x == 0) s_st = read_step_start(a.pol, a.ctrl);
   __syncthreads();
   const StepStart st = s_st;
-  S lam_loc = (S)0;
+  typename Ops<A>::P lam_loc = 0;
   unsigned bad = 0u;
 
   if (st.run) {
@@ -748,8 +786,8 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
     const S *__restrict__ src = (n & 1) ? a.buf1 : a.buf0;
     S *__restrict__ dst = (n & 1) ? a.buf0 : a.buf1;
     const SysParams<A> P = splat_params<A>(a.sp);
-    const A lx = Ops<A>::splat((S)(st.dt / a.dx));
-    const A ly = Ops<A>::splat((S)(st.dt / a.dy));
+    const A lx = Ops<A>::splat((typename Ops<A>::P)(st.dt / a.dx));
+    const A ly = Ops<A>::splat((typename Ops<A>::P)(st.dt / a.dy));
     const bool writer = lane >= 1 && lane <= 30;
     const int gw = blockIdx.x * NW + warp;
     const int GW = gridDim.x * NW;

@@ -28,6 +28,10 @@ void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT(float, 1, 2, 64, 4, 5, 4, "euler f32 v2 ty64 w4 b5 tma4");
   FV_VARIANT(float, 1, 1, 64, 4, 8, 0, "euler f32 v1 ty64 w4 b8");
   FV_VARIANT(F2, 1, 1, 64, 4, 4, -6, "euler f32 x2 v1 ty64 w4 b4 async6");
+  FV_VARIANT(BF, 2, 2, 64, 4, 5, -6, "euler bf16 v2 ty64 w4 b5 async6");
+  FV_VARIANT(BF, 2, 4, 64, 4, 4, -6, "euler bf16 v4 ty64 w4 b4 async6");
+  FV_VARIANT(BF, 2, 4, 64, 4, 4, 0, "euler bf16 v4 ty64 w4 b4");
+  FV_VARIANT(BF, 2, 2, 64, 4, 5, 0, "euler bf16 v2 ty64 w4 b5");
 }
 
 }  // namespace fv

@@ -19,13 +19,13 @@ from . import build as _build
 FV_OK, FV_ERR_INVALID_ARG, FV_ERR_CUDA, FV_ERR_OOM = 0, 1, 2, 3
 FV_ERR_CFL, FV_ERR_NONPHYSICAL, FV_ERR_TIMEOUT, FV_ERR_STATE = 4, 5, 6, 7
 FV_ADVECTION, FV_EULER, FV_SPRAY = 0, 1, 2
-FV_F64, FV_F32 = 0, 1
+FV_F64, FV_F32, FV_BF16 = 0, 1, 2
 FV_BC_PERIODIC, FV_BC_TRANSMISSIVE, FV_BC_DIRICHLET = 0, 1, 2
 FV_CONSERVED, FV_PRIMITIVE = 0, 1
 
 SYSTEMS = {"advection": FV_ADVECTION, "euler": FV_EULER, "spray": FV_SPRAY}
 BCS = {"periodic": FV_BC_PERIODIC, "transmissive": FV_BC_TRANSMISSIVE, "dirichlet": FV_BC_DIRICHLET}
-PRECISIONS = {"f64": FV_F64, "f32": FV_F32}
+PRECISIONS = {"f64": FV_F64, "f32": FV_F32, "bf16": FV_BF16}
 NVAR = {FV_ADVECTION: 1, FV_EULER: 4, FV_SPRAY: 6}
 
 

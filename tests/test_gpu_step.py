@@ -95,6 +95,26 @@ def test_euler_parity_ragged(bc, precision):
         assert abs(t - ref.t) <= 1e-5 * ref.t
 
 
+def test_bf16_storage_error_bound():
+    """bfloat16 storage, FP32 arithmetic: every stored value is rounded to
+    8 significant bits (unit roundoff 2^-9 = 2.0e-3).  The first-order scheme
+    damps the accumulated rounding, so the relative L1 error stays of the
+    order of the unit roundoff: bound 1e-2 after 60 steps on smooth data, and
+    the conserved totals drift by less than 1e-3 relative."""
+    prim, d = wl.random_smooth_euler(193, seed=23, ny=141)
+    ref = oracle_run(d, prim, 60)
+    out, t, _ = gpu_run(d, prim, 60, "bf16")
+    l1 = rel_l1(out, ref.W)
+    print("bf16 rel L1 per variable", l1, "rel Linf", rel_linf(out, ref.W))
+    assert l1.max() <= 1e-2, l1
+    assert abs(t - ref.t) <= 1e-2 * ref.t
+    P = oracle_problem(d)
+    t0 = oracle.totals(P, oracle.prim_to_cons(P, prim))
+    t1 = oracle.totals(P, out)
+    mass = np.abs(ref.W).sum(axis=(1, 2)) * P.dx * P.dy
+    assert np.all(np.abs(t1 - t0) / mass <= 1e-3)
+
+
 def test_four_quadrant_512_parity_and_symmetry():
     """The four-quadrant Riemann problem (transmissive, 8 x 8 subdomains) at
     512^2 for 500 steps; the exact solution is transpose symmetric and so is
@@ -106,7 +126,14 @@ def test_four_quadrant_512_parity_and_symmetry():
     assert np.array_equal(transpose_state(out, "euler"), out)
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+def to_bf16(x):
+    """Round float64 values to the nearest bfloat16 (ties to even), as float64."""
+    f = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((f + 0x7FFF + ((f >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
 def test_every_kernel_variant_gives_the_same_bits(precision):
     """Tile shape, cells per lane and warps per block change only the work
     decomposition: every candidate returns identical bits."""
@@ -124,22 +151,26 @@ def test_degenerate_and_odd_grids(shape):
     prim, d = wl.random_smooth_euler(nx, seed=3, ny=ny)
     d = dict(d, bc=("transmissive", "periodic", "transmissive", "periodic"))
     ref = oracle_run(d, prim, 9)
-    for precision in ("f64", "f32"):
+    for precision in ("f64", "f32", "bf16"):
         for k in range(n_variants("euler", precision)):
             out, _, _ = gpu_run(d, prim, 9, precision, tune=2 + k)
             if precision == "f64":
                 assert rel_linf(out, ref.W).max() <= 1e-12, (shape, k)
-            else:
+            elif precision == "f32":
                 assert rel_linf(out, ref.W).max() <= 1e-5, (shape, k)
+            else:
+                assert rel_linf(out, ref.W).max() <= 2e-2, (shape, k)
 
 
 # ------------------------------------------------------------------ invariants
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("bc", ["periodic", "transmissive", "dirichlet"])
 def test_constant_state_bitwise(precision, bc):
     const = np.array([1.3, 0.4 * 1.3, -0.25 * 1.3, 2.5])
     if precision == "f32":
         const = const.astype(np.float32).astype(np.float64)
+    if precision == "bf16":
+        const = to_bf16(const)
     W0 = np.empty((4, 37, 45))
     for v in range(4):
         W0[v] = const[v]
@@ -175,7 +206,7 @@ def test_totals_match_compensated_sum():
     assert np.all(np.abs(tot - ref) <= 1e-15 * np.abs(W).sum(axis=(1, 2)) * P.dx * P.dy)
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
 def test_transposition_bitwise(precision):
     prim, d = wl.random_smooth_euler(83, seed=7, ny=54)
     d = dict(d, bc=("transmissive", "periodic", "transmissive", "periodic"))
@@ -183,6 +214,8 @@ def test_transposition_bitwise(precision):
     W0 = oracle.prim_to_cons(P, prim)
     if precision == "f32":
         W0 = W0.astype(np.float32).astype(np.float64)
+    if precision == "bf16":
+        W0 = to_bf16(W0)
     out, _, _ = gpu_run(d, W0, 30, precision, primitive=False)
     dt_ = dict(d, nx=54, ny=83, bc=("periodic", "transmissive", "periodic", "transmissive"))
     outt, _, _ = gpu_run(dt_, transpose_state(W0, "euler"), 30, precision, primitive=False)
