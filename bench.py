@@ -111,6 +111,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def measured_traffic_per_cell(kernel_desc: str):
+    """DRAM bytes per cell-update of a kernel, from the ncu capture recorded
+    next to the profile summaries (None when that kernel was not captured)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if line.startswith("#") or "|" not in line:
+                    continue
+                desc, val = (x.strip() for x in line.split("|", 1))
+                if desc == kernel_desc:
+                    return float(val)
+    except OSError:
+        pass
+    return None
+
+
 def max_over_ranks(value: float, device: str = "cpu") -> float:
     """Largest value over all ranks (the slowest rank's time); identity on one
     process.  device: where the reduction tensor lives ("cuda:k" for NCCL,
@@ -365,7 +384,10 @@ def main():
                       "kernel": kinfo32, "l2": "inputs larger than L2 (state buffers 1 GiB f32 / 2 GiB f64)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm, "unit": "GB/s",
-                        "frac": achieved32 / hbm, "traffic": None,
+                        "frac": achieved32 / hbm,
+                        "traffic": (None if measured_traffic_per_cell(kinfo32) is None
+                                    else measured_traffic_per_cell(kinfo32) * ncell),
+                        "traffic_source": "ncu dram__bytes_read+write of this kernel on 4096^2, scaled by cells",
                         "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                         "algorithmic_bytes_per_launch": algo_bytes_32,
                         "avg_launch_us": avg_launch_s * 1e6},
