@@ -82,12 +82,24 @@ static __device__ bool wait_at_least(const unsigned *flag, unsigned target, long
   }
 }
 
-template <class Sys, class R, int V, int TY, int NW, int MINB>
+// D = 0: register prefetch with L2 loads (ld.cg).  D < 0: rows staged through
+// a per-lane cp.async ring of -D slots (dynamic shared memory), as in the
+// single-instance kernel.  Both may read data written earlier in the same
+// launch: a warp starts a task only after lane 0's acquire load has seen the
+// step released (the release follows every write of the previous step) and
+// __syncwarp has ordered that acquire before the other lanes' loads, so the
+// memory model guarantees that no load, cached or asynchronous, sees stale
+// values.
+template <class Sys, class R, int V, int TY, int NW, int MINB, int D = 0>
 __global__ void __launch_bounds__(NW * 32, MINB)
 fv_batch_kernel(const BatchArgs<R> b) {
   __shared__ StepArgs<R> s_args[NW];
+  extern __shared__ __align__(128) unsigned char s_dyn[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   StepArgs<R> &a = s_args[warp];
+  constexpr int DA = D < 0 ? -D : 2;
+  LaneRing<R, V, Sys::NV, DA> lrg;
+  if (D < 0) lrg.buf = reinterpret_cast<R *>(s_dyn) + warp * (DA * Sys::NV * 32 * V) + lane * V;
   const unsigned total = (unsigned)b.nsteps * (unsigned)b.T;
   const bool writer = lane >= 1 && lane <= 30;
   int cur_inst = -1;
@@ -103,6 +115,7 @@ fv_batch_kernel(const BatchArgs<R> b) {
     int ok = 1;
     if (lane == 0) ok = wait_at_least(&b.rc[i].released, s, b.timeout_ns, b.abort) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
     if (!ok) break;
     if (i != cur_inst) {
       const unsigned *src = reinterpret_cast<const unsigned *>(&b.inst[i]);
@@ -129,18 +142,22 @@ fv_batch_kernel(const BatchArgs<R> b) {
       const R *src = (n & 1) ? a.buf1 : a.buf0;
       R *dst = (n & 1) ? a.buf0 : a.buf1;
       const SysParams<R> P = a.sp;
-      const R lx = (R)(dt / a.dx), ly = (R)(dt / a.dy);
+      // half steps: the face fluxes are carried doubled (see lf_face2)
+      const R lx = (R)(0.5 * (dt / a.dx)), ly = (R)(0.5 * (dt / a.dy));
       const int strip = lt % a.nstrips, chunk = lt / a.nstrips;
       const int X = strip * (30 * V) + (lane - 1) * V;
       const int y0 = chunk * TY, y1 = min(y0 + TY, a.ny);
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
-      if (xin) march<Sys, R, V, true, true, true>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      if (D < 0 && xin) march_async<Sys, R, V, DA, true, true>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (D < 0) march_async<Sys, R, V, DA, true, false>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (xin) march<Sys, R, V, true, true, true>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else march<Sys, R, V, false, true, true>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }
     double l = (double)lam_loc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
     const int anybad = __any_sync(0xffffffffu, bad != 0u);
+    __syncwarp();  // every lane's stores of this task precede lane 0's fence below
     if (lane == 0) {
       if (run) {
         if (anybad) atomicMax(&ic->lam[(n + 1) % 3], 0x7ff8000000000000ull);
@@ -173,23 +190,31 @@ fv_batch_kernel(const BatchArgs<R> b) {
 
 struct BatchVariant {
   int system, precision, V, TY, NW;
+  int smem;  // dynamic shared memory per block (cp.async ring)
   const void *kernel;
   const char *desc;
 };
 
-#define FV_BVARIANT(SYS, SYSID, R, PREC, V, TY, NW, MB, DESC)                                      \
+#define FV_BVARIANT(SYS, SYSID, R, PREC, V, TY, NW, MB, D, DESC)                                   \
   out.push_back(BatchVariant{SYSID, PREC, V, TY, NW,                                              \
-                             reinterpret_cast<const void *>(&fv_batch_kernel<SYS, R, V, TY, NW, MB>), DESC})
+                             (D) < 0 ? async_smem_bytes<R, V, SYS::NV, ((D) < 0 ? -(D) : 2)>(NW) : 0,     \
+                             reinterpret_cast<const void *>(&fv_batch_kernel<SYS, R, V, TY, NW, MB, D>), DESC})
 
 static const std::vector<BatchVariant> &batch_variants() {
   static std::vector<BatchVariant> out;
   if (out.empty()) {
-    FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, "batch euler f32 v1 ty64 w4 b6");
-    FV_BVARIANT(Euler, kEuler, float, 1, 1, 128, 4, 6, "batch euler f32 v1 ty128 w4 b6");
-    FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 4, "batch euler f32 v2 ty64 w4 b4");
-    FV_BVARIANT(Euler, kEuler, double, 0, 1, 32, 4, 4, "batch euler f64 v1 ty32 w4 b4");
-    FV_BVARIANT(Advection, kAdvection, double, 0, 1, 32, 4, 4, "batch advection f64 v1 ty32 w4 b4");
-    FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, "batch advection f32 v1 ty64 w4 b6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, -6, "batch euler f32 v1 ty64 w4 b6 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 4, -6, "batch euler f32 v2 ty64 w4 b4 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, -4, "batch euler f32 v1 ty64 w4 b6 async4");
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 32, 4, 6, -6, "batch euler f32 v1 ty32 w4 b6 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 5, 0, "batch euler f32 v1 ty64 w4 b5");
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 128, 4, 5, 0, "batch euler f32 v1 ty128 w4 b5");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 3, 0, "batch euler f32 v2 ty64 w4 b3");
+    FV_BVARIANT(Euler, kEuler, double, 0, 1, 32, 4, 3, 0, "batch euler f64 v1 ty32 w4 b3");
+    FV_BVARIANT(Euler, kEuler, double, 0, 1, 64, 4, 4, -4, "batch euler f64 v1 ty64 w4 b4 async4");
+    FV_BVARIANT(Advection, kAdvection, double, 0, 1, 32, 4, 4, 0, "batch advection f64 v1 ty32 w4 b4");
+    FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, 0, "batch advection f32 v1 ty64 w4 b6");
+    FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, -6, "batch advection f32 v1 ty64 w4 b6 async6");
   }
   return out;
 }
@@ -222,6 +247,7 @@ struct fv_batch {
   int sms = 0;
   long long timeout_ns = 2000000000LL;
   int skip_release = -1;
+  bool tuned = false;
   void *staging = nullptr;
   size_t staging_bytes = 0;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
@@ -332,8 +358,10 @@ static fv_status batch_select(fv_batch *b, int vi) {
   FV_BCUDA(b, cudaMemcpy(b->task_inst, tinst.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
   FV_BCUDA(b, cudaMemcpy(b->task_base, tbase.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
   FV_BCUDA(b, cudaMemcpy(b->d_args, args.data(), asz * b->n, cudaMemcpyHostToDevice));
+  if (V.smem > 48 * 1024)
+    FV_BCUDA(b, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
   int nb = 0;
-  FV_BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, 0));
+  FV_BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));
   if (nb < 1) return bfail(b, FV_ERR_CUDA, "batched kernel cannot launch");
   b->grid = nb * b->sms;
   b->T = T;
@@ -520,11 +548,11 @@ static fv_status batch_graph(fv_batch *b, int nsteps, cudaGraphExec_t *out) {
     if (b->prec == 0) {
       BatchArgs<double> a = make_batch_args<double>(b, nsteps);
       void *args[] = {&a};
-      e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, 0, b->cap_stream);
+      e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, V.smem, b->cap_stream);
     } else {
       BatchArgs<float> a = make_batch_args<float>(b, nsteps);
       void *args[] = {&a};
-      e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, 0, b->cap_stream);
+      e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, V.smem, b->cap_stream);
     }
   }
   cudaGraph_t g = nullptr;
@@ -543,6 +571,69 @@ static fv_status batch_graph(fv_batch *b, int nsteps, cudaGraphExec_t *out) {
   return FV_OK;
 }
 
+// Autotuner (tune = 1): before the first run, time one step of every
+// candidate kernel of this system and precision on the batch's own state and
+// keep the fastest (median of three timings after one warm-up).  A timed step
+// writes only the buffers that the next step overwrites, and the control
+// blocks are put back after every timing, so states, times and step counts
+// are unchanged.
+static fv_status batch_autotune(fv_batch *b) {
+  fv_status st = read_ictrl(b);
+  if (st != FV_OK) return st;
+  const std::vector<Ctrl> saved(b->h_ictrl, b->h_ictrl + b->n);
+  auto restore = [&]() -> fv_status {
+    std::memcpy(b->h_ictrl, saved.data(), sizeof(Ctrl) * b->n);
+    FV_BCUDA(b, cudaMemcpyAsync(b->ictrl, b->h_ictrl, sizeof(Ctrl) * b->n, cudaMemcpyHostToDevice, b->stream));
+    return FV_OK;
+  };
+  const auto &vs = batch_variants();
+  std::vector<int> cand;
+  for (size_t k = 0; k < vs.size(); ++k)
+    if (vs[k].system == b->system && vs[k].precision == b->prec) cand.push_back((int)k);
+  cudaEvent_t e0, e1;
+  FV_BCUDA(b, cudaEventCreate(&e0));
+  FV_BCUDA(b, cudaEventCreate(&e1));
+  int best = b->variant;
+  float best_ms = 1e30f;
+  for (int vi : cand) {
+    if ((st = batch_select(b, vi)) != FV_OK) break;
+    cudaGraphExec_t g;
+    if ((st = batch_graph(b, 1, &g)) != FV_OK) break;
+    std::vector<float> ms;
+    for (int rep = 0; rep < 4 && st == FV_OK; ++rep) {
+      if ((st = restore()) != FV_OK) break;
+      cudaError_t e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(g, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_abort, b->runblock + sizeof(RunCounters) * b->n + sizeof(unsigned),
+                                                sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e != cudaSuccess) st = bfail(b, FV_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+      else if (*b->h_abort & kErrTimeout) st = bfail(b, FV_ERR_TIMEOUT, "a batched-step wait timed out");
+      else if (rep > 0) ms.push_back(t);
+    }
+    if (st != FV_OK) break;
+    std::sort(ms.begin(), ms.end());
+    if (ms[ms.size() / 2] < best_ms) {
+      best_ms = ms[ms.size() / 2];
+      best = vi;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const fv_status rs = restore();
+  if (st == FV_OK) st = rs;
+  if (st == FV_OK) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) st = bfail(b, FV_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  }
+  if (st != FV_OK) return st;
+  b->tuned = true;
+  return batch_select(b, best);
+}
+
 extern "C" fv_status fv_batch_run(fv_batch *b, int nsteps) {
   if (!b) return FV_ERR_INVALID_ARG;
   if (nsteps < 0) return bfail(b, FV_ERR_INVALID_ARG, "nsteps < 0");
@@ -552,6 +643,10 @@ extern "C" fv_status fv_batch_run(fv_batch *b, int nsteps) {
   // tickets of one run must fit the 32-bit counter
   if ((unsigned long long)nsteps * (unsigned long long)b->T >= (1ull << 31))
     return bfail(b, FV_ERR_INVALID_ARG, "too many steps in one run");
+  if (b->cfg[0].tune == 1 && !b->tuned) {
+    fv_status st = batch_autotune(b);
+    if (st != FV_OK) return st;
+  }
   cudaGraphExec_t g;
   fv_status st = batch_graph(b, nsteps, &g);
   if (st != FV_OK) return st;

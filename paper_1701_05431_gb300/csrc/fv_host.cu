@@ -157,6 +157,46 @@ static int default_variant(int system, int prec) {
   return -1;
 }
 
+// Blocks of a kernel candidate resident per SM (its register target MINB if
+// the occupancy query fails).
+static int resident_blocks(const Variant &V) {
+  if (V.smem > 48 * 1024 &&
+      cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem) != cudaSuccess)
+    return V.MINB;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem) != cudaSuccess || nb < 1)
+    return V.MINB;
+  return nb;
+}
+
+// Default kernel for an nx x ny grid: the first candidate of (system,
+// precision), unless its warp tasks cannot fill the GPU (fewer than two per
+// resident warp).  Then the candidate with the same lane width, warps,
+// register target and staging but shorter tasks: the tallest one that fills
+// the GPU, else the shortest.
+static int default_variant_for(int system, int prec, int nx, int ny, int sms) {
+  const int d = default_variant(system, prec);
+  if (d < 0) return d;
+  const auto &vs = all_variants();
+  const long long warps = (long long)resident_blocks(vs[d]) * vs[d].NW * sms;
+  auto fills = [&](const Variant &V) {
+    const long long tasks = (long long)((nx + 30 * V.V - 1) / (30 * V.V)) * ((ny + V.TY - 1) / V.TY);
+    return tasks >= 2LL * warps;
+  };
+  if (fills(vs[d])) return d;
+  int pick = d;
+  for (size_t k = 0; k < vs.size(); ++k) {
+    const Variant &V = vs[k], &D0 = vs[d];
+    if (V.system != system || V.precision != prec || V.V != D0.V || V.NW != D0.NW || V.MINB != D0.MINB ||
+        V.D != D0.D || V.TY >= D0.TY)
+      continue;
+    const Variant &P = vs[pick];
+    const bool pf = pick != d && fills(P), vf = fills(V);
+    if (pick == d || (vf && (!pf || V.TY > P.TY)) || (!vf && !pf && V.TY < P.TY)) pick = (int)k;
+  }
+  return pick;
+}
+
 static std::vector<int> candidates(int system, int prec) {
   std::vector<int> out;
   const auto &vs = all_variants();
@@ -381,7 +421,7 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, c->sms);
   }
   int prec = cfg->precision;  // 0 f64, 1 f32, 2 bf16 storage
-  int vi = default_variant(cfg->system, prec);
+  int vi = default_variant_for(cfg->system, prec, cfg->nx, cfg->ny, c->sms);
   if (cfg->tune >= 2) {
     auto cand = candidates(cfg->system, prec);
     if (cfg->tune - 2 >= (int)cand.size()) {

@@ -15,11 +15,11 @@ namespace fv {
 struct Variant {
   int system;      // kAdvection / kEuler / kSpray
   int precision;   // 0: f64, 1: f32
-  int V;           // cells per lane along x
+  int V;           // cells per lane along x (values per lane x cells per value)
   int TY;          // rows per warp task
   int NW;          // warps per block
   int MINB;        // blocks per SM the register budget is cut for
-  int D;           // TMA ring depth (0: register prefetch only)
+  int D;           // row staging: 0 register prefetch, > 0 TMA ring depth, < 0 cp.async ring depth
   int smem;        // dynamic shared memory per block (bytes)
   const void *kernel;
   const char *desc;

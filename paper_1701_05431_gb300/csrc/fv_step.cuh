@@ -239,12 +239,12 @@ static __device__ __forceinline__ void row_x(const SysParams<A> &P, const A (&W)
     // values of the cells just west of this value's cells
     const A sprev = c == 0 ? O::shfl_up(sx[V - 1], 1) : sx[c - 1];
     const A sL = O::shift_in(sprev, sx[c]);
-    const A hs = O::mul(O::splat(0.5), O::max(sL, sx[c]));
+    const A sg = O::max(sL, sx[c]);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const A wprev = c == 0 ? O::shfl_up(W[V - 1][v], 1) : W[c - 1][v];
       const A fprev = c == 0 ? O::shfl_up(Fx[V - 1][v], 1) : Fx[c - 1][v];
-      Fw[c][v] = lf_face(O::shift_in(wprev, W[c][v]), O::shift_in(fprev, Fx[c][v]), W[c][v], Fx[c][v], hs);
+      Fw[c][v] = lf_face2(O::shift_in(wprev, W[c][v]), O::shift_in(fprev, Fx[c][v]), W[c][v], Fx[c][v], sg);
     }
   }
 #pragma unroll
@@ -282,10 +282,10 @@ static __device__ __forceinline__ void advance_row(const StepArgs<typename Ops<A
   A Wn[V][NV];
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    const A hs = O::mul(O::splat(0.5), O::max(cur.sy[c], nxt.sy[c]));
+    const A sg = O::max(cur.sy[c], nxt.sy[c]);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const A Fn = lf_face(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], hs);
+      const A Fn = lf_face2(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], sg);
       Wn[c][v] = fv_update(cur.W[c][v], cur.dX[c][v], O::sub(Fn, Fs[c][v]), lx, ly);
       Fs[c][v] = Fn;
     }
@@ -380,9 +380,9 @@ static __device__ __forceinline__ void march(const StepArgs<typename Ops<A>::S> 
   row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    const A hs = O::mul(O::splat(0.5), O::max(RA.sy[c], RB.sy[c]));
+    const A sg = O::max(RA.sy[c], RB.sy[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], hs);
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
   }
   // the two row states swap roles every row (unrolled by two: no copies)
   int j = y0;
@@ -563,9 +563,9 @@ static __device__ __forceinline__ void march_tma(const StepArgs<typename Ops<A>:
   row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    const A hs = O::mul(O::splat(0.5), O::max(RA.sy[c], RB.sy[c]));
+    const A sg = O::max(RA.sy[c], RB.sy[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], hs);
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
   }
   int j = y0;
   while (true) {
@@ -623,9 +623,15 @@ template <class S, int N, int NV, int D> struct LaneRing {
   __device__ __forceinline__ S *slot(int s, int v) const { return buf + ((s * NV + v) * 32) * N; }
 };
 
-template <class A, int V, int NV, int D>
+// Issue the copies of row j into ring slot r % D.  Interior strips (XIN)
+// copy each lane's N contiguous cells per variable; strips at the east or
+// west boundary map every cell through lane_cols: a real or ghost column is
+// copied on its own (4 or 8 bytes; 2-byte cells are loaded and stored
+// directly), a Dirichlet ghost value is stored directly.  Direct stores land
+// in the lane's own slots, so program order makes them visible to its reads.
+template <class A, int V, int NV, int D, bool XIN>
 static __device__ __forceinline__ void lring_issue(const StepArgs<typename Ops<A>::S> &a,
-                                                   const typename Ops<A>::S *__restrict__ src_lane,
+                                                   const typename Ops<A>::S *__restrict__ src, int X,
                                                    const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
                                                    int r, int j) {
   using S = typename Ops<A>::S;
@@ -638,10 +644,22 @@ static __device__ __forceinline__ void lring_issue(const StepArgs<typename Ops<A
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = (S)a.bc_state[dir][v];
-  } else {
-    const S *g = src_lane + (long long)sj * a.pitch;
+  } else if (XIN) {
+    const S *g = src + X + (long long)sj * a.pitch;
 #pragma unroll
     for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), g + v * a.plane);
+  } else {
+    const LaneCols<N> L = lane_cols<N>(a, X);
+    const S *g = src + (long long)sj * a.pitch;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        S *d = rg.slot(slot, v) + c;
+        if (L.dir[c] >= 0) *d = (S)a.bc_state[L.dir[c]][v];
+        else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, g + v * a.plane + L.col[c]);
+        else *d = __ldcg(g + v * a.plane + L.col[c]);
+      }
   }
   cp_async_commit();
 }
@@ -659,12 +677,13 @@ static __device__ __forceinline__ void lring_read(const LaneRing<typename Ops<A>
   }
 }
 
-// March one interior warp task through the per-lane cp.async ring.  Rows
+// March one warp task through the per-lane cp.async ring (XIN: interior
+// strip, every lane's cells inside the grid).  Rows
 // are numbered r = 0 .. nrows - 1 (row y0 - 1 + r); before reading row r the
 // lane has issued rows up to r + D - 2 and waits until at most D - 2 copy
 // groups are pending, i.e. row r has landed.  A slot is refilled only after
 // the row read from it has been consumed by the flux computation.
-template <class Sys, class A, int V, int D, bool FIN>
+template <class Sys, class A, int V, int D, bool FIN, bool XIN>
 static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
                                                    const typename Ops<A>::S *__restrict__ src,
                                                    typename Ops<A>::S *__restrict__ dst,
@@ -674,13 +693,12 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV;
   using O = Ops<A>;
-  const S *src_lane = src + X;
   S *dst_lane = dst + X;
   const int nrows = y1 - y0 + 2;
   // prologue: rows 0 .. D-2 in flight (empty groups past the end keep the count)
 #pragma unroll
   for (int r = 0; r < D - 1; ++r) {
-    if (r < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, r, y0 - 1 + r);
+    if (r < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, r, y0 - 1 + r);
     else cp_async_commit();
   }
   RowState<A, V, NV> RA, RB;
@@ -692,18 +710,18 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
     A Fx_[NV], sx_;
     Sys::fluxes(RA.W[c], P, Fx_, sx_, RA.Fy[c], RA.sy[c]);
   }
-  if (D - 1 < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, D - 1, y0 - 1 + D - 1);
+  if (D - 1 < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, D - 1, y0 - 1 + D - 1);
   else cp_async_commit();
   cp_async_wait<D - 2>();
   lring_read<A, V, NV, D>(rg, 1, RB.W);
   row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
-  if (D < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, D, y0 - 1 + D);
+  if (D < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, D, y0 - 1 + D);
   else cp_async_commit();
 #pragma unroll
   for (int c = 0; c < V; ++c) {
-    const A hs = O::mul(O::splat(0.5), O::max(RA.sy[c], RB.sy[c]));
+    const A sg = O::max(RA.sy[c], RB.sy[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], hs);
+    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
   }
   int j = y0;
   while (true) {
@@ -712,8 +730,8 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       lring_read<A, V, NV, D>(rg, r, RA.W);
-      advance_row<Sys, A, V, true, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad);
-      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
+      advance_row<Sys, A, V, XIN, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad);
+      if (r + D - 1 < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -722,8 +740,8 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       lring_read<A, V, NV, D>(rg, r, RB.W);
-      advance_row<Sys, A, V, true, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad);
-      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src_lane, rg, r + D - 1, y0 - 1 + r + D - 1);
+      advance_row<Sys, A, V, XIN, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad);
+      if (r + D - 1 < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -786,8 +804,9 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
     const S *__restrict__ src = (n & 1) ? a.buf1 : a.buf0;
     S *__restrict__ dst = (n & 1) ? a.buf0 : a.buf1;
     const SysParams<A> P = splat_params<A>(a.sp);
-    const A lx = Ops<A>::splat((typename Ops<A>::P)(st.dt / a.dx));
-    const A ly = Ops<A>::splat((typename Ops<A>::P)(st.dt / a.dy));
+    // half steps: the face fluxes are carried doubled (see lf_face2)
+    const A lx = Ops<A>::splat((typename Ops<A>::P)(0.5 * (st.dt / a.dx)));
+    const A ly = Ops<A>::splat((typename Ops<A>::P)(0.5 * (st.dt / a.dy)));
     const bool writer = lane >= 1 && lane <= 30;
     const int gw = blockIdx.x * NW + warp;
     const int GW = gridDim.x * NW;
@@ -800,7 +819,8 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
       // warp-uniform: does every lane of the strip read real columns only?
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
       if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (D < 0 && xin) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (D < 0 && xin) march_async<Sys, A, V, DA, FIN, true>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (D < 0) march_async<Sys, A, V, DA, FIN, false>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else if (xin) march<Sys, A, V, true, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else march<Sys, A, V, false, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }

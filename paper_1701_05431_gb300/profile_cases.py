@@ -1,0 +1,81 @@
+"""Small, self-contained invocations of each kernel, for profiling with ncu.
+
+  python -m paper_1701_05431_gb300.profile_cases step --system euler --precision f32 --n 4096 --steps 3
+  python -m paper_1701_05431_gb300.profile_cases batch --instances 96 --steps 4 --tune 2
+  python -m paper_1701_05431_gb300.profile_cases spray --precision f64 --n 1024 --steps 3
+
+Each case builds its seeded synthetic input (the `workloads` generators),
+copies it to the device, sets the state through the C ABI and advances the
+given number of time steps once; nothing is timed.  `--tune K` (K >= 2) forces
+kernel candidate K - 2, so that a capture sees a known kernel.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _device(a):
+    import numpy as np
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def step_case(system: str, precision: str, n: int, steps: int, tune: int) -> str:
+    import torch
+    import workloads as wl
+    from paper_1701_05431_gb300 import fvlib
+    if system == "euler":
+        prim, d = wl.smooth_periodic(n)
+    elif system == "advection":
+        prim, d = wl.advection_bump(n)
+    else:
+        prim, d = wl.spray_field(n)
+    stream = torch.cuda.current_stream().cuda_stream
+    with fvlib.Solver(d, precision, stream=stream, tune=tune) as s:
+        s.set_state(_device(prim), primitive=True)
+        s.run(steps)
+        torch.cuda.synchronize()
+        return s.kernel_info()[1]
+
+
+def batch_case(instances: int, steps: int, tune: int, precision: str = "f32") -> str:
+    import torch
+    import workloads as wl
+    from paper_1701_05431_gb300 import fvlib
+    insts = wl.batched_quadrants(instances)
+    stream = torch.cuda.current_stream().cuda_stream
+    with fvlib.Batch([d for _, _, d in insts], precision, stream=stream, tune=tune) as b:
+        for k, (_, prim, _) in enumerate(insts):
+            b.set_state(k, prim, primitive=True)
+        b.run(steps)
+        torch.cuda.synchronize()
+        return b.kernel_info()[1]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("case", choices=["step", "batch", "spray"])
+    ap.add_argument("--system", default="euler", choices=["euler", "advection"])
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--instances", type=int, default=96)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--tune", type=int, default=0)
+    a = ap.parse_args(argv)
+    if a.case == "step":
+        k = step_case(a.system, a.precision, a.n, a.steps, a.tune)
+    elif a.case == "spray":
+        k = step_case("spray", a.precision, a.n, a.steps, a.tune)
+    else:
+        k = batch_case(a.instances, a.steps, a.tune, "f32" if a.precision == "bf16" else a.precision)
+    print(f"{a.case}: {k}")
+
+
+if __name__ == "__main__":
+    main()

@@ -95,6 +95,18 @@ def test_batch_every_candidate_same_bits():
             assert np.array_equal(a, b)
 
 
+def test_batch_autotuner_keeps_state_time_and_bits():
+    """tune = 1 times one step of every candidate on the batch's own state
+    before the first run; the control blocks are put back, so the results,
+    times and step counts equal those of the untuned run."""
+    insts = small_batch(6, seed=13)
+    base, tb = run_batch(insts, 15, "f32", tune=0)
+    tuned, tt = run_batch(insts, 15, "f32", tune=1)
+    for a, b in zip(tuned, base):
+        assert np.array_equal(a, b)
+    assert tt == tb
+
+
 def test_batch_c4_distribution_fp32_vs_oracle():
     """64 instances drawn like the 512 of the batched workload (sizes 64..1024,
     random four-quadrant states), 200 steps in one launch; the three smallest
