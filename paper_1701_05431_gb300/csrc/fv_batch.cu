@@ -37,9 +37,21 @@ struct RunCounters {
   unsigned released;  // steps of this instance open during this run (step s needs released >= s)
 };
 
+// The dt decision of one step of one instance, made once by the warp that
+// closes the previous step (lmax(W^n) is complete then), so that the warps
+// of step n read it instead of each repeating the FP64 divisions.
+struct StepPlan {
+  long long step;  // the step this plan is for (-1: none)
+  double dt;
+  double hx, hy;   // dt / (2 dx), dt / (2 dy): the update's factors (doubled face fluxes)
+  int run;
+  unsigned err;
+};
+
 template <class R> struct BatchArgs {
   const StepArgs<R> *inst;   // per-instance geometry, buffers, dt policy, BCs
   Ctrl *ictrl;               // per-instance lmax slots, t, step, error flags
+  StepPlan *plan;            // per-instance dt decision of its next step
   RunCounters *rc;           // per-instance counters of this run
   const int *task_inst;      // T entries: instance of each task of a step
   const int *task_base;      // first task of each instance within a step
@@ -125,37 +137,59 @@ fv_batch_kernel(const BatchArgs<R> b) {
       cur_inst = i;
     }
     Ctrl *ic = &b.ictrl[i];
-    // dt of this step of instance i (same rule as the single-instance kernel)
-    Ctrl c;
-    c.step = __ldcg(&ic->step);
-    c.t = __ldcg(&ic->t);
-    c.t_end = 0.0;
-    c.err_committed = __ldcg(&ic->err_committed);
-    const double lam = lam_value(__ldcg(&ic->lam[c.step % 3]));
-    double dt = 0.0;
+    // dt of this step of instance i (same rule as the single-instance kernel):
+    // from the plan the previous step's closing warp left, else computed here
+    // (the first step of a run)
+    const long long n = __ldcg(&ic->step);
+    double dt = 0.0, hx = 0.0, hy = 0.0;
     unsigned err = 0u;
-    const bool run = choose_dt(a.pol, c, lam, &dt, &err);
+    bool run;
+    if (__ldcg(&b.plan[i].step) == n) {
+      run = __ldcg(&b.plan[i].run) != 0;
+      err = __ldcg(&b.plan[i].err);
+      dt = __ldcg(&b.plan[i].dt);
+      hx = __ldcg(&b.plan[i].hx);
+      hy = __ldcg(&b.plan[i].hy);
+    } else {
+      Ctrl c;
+      c.step = n;
+      c.t = __ldcg(&ic->t);
+      c.t_end = 0.0;
+      c.err_committed = __ldcg(&ic->err_committed);
+      run = choose_dt(a.pol, c, lam_value(__ldcg(&ic->lam[n % 3])), &dt, &err);
+      hx = 0.5 * (dt / a.dx);
+      hy = 0.5 * (dt / a.dy);
+    }
     R lam_loc = (R)0;
     unsigned bad = 0u;
-    const long long n = c.step;
     if (run) {
+      // the instance's geometry in registers (see MarchGeo)
+      MarchGeo<R> g;
+      g.ctrl = a.ctrl;
+      g.nx = a.nx;
+      g.ny = a.ny;
+      g.pitch = a.pitch;
+      g.plane = a.plane;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g.bc[q] = a.bc[q];
+      g.bc_state = a.bc_state;
       const R *src = (n & 1) ? a.buf1 : a.buf0;
       R *dst = (n & 1) ? a.buf0 : a.buf1;
       const SysParams<R> P = a.sp;
       // half steps: the face fluxes are carried doubled (see lf_face2)
-      const R lx = (R)(0.5 * (dt / a.dx)), ly = (R)(0.5 * (dt / a.dy));
+      const R lx = (R)hx, ly = (R)hy;
       const int strip = lt % a.nstrips, chunk = lt / a.nstrips;
       const int X = strip * (30 * V) + (lane - 1) * V;
-      const int y0 = chunk * TY, y1 = min(y0 + TY, a.ny);
-      const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= a.nx);
-      if (D < 0 && xin) march_async<Sys, R, V, DA, true, true>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (D < 0) march_async<Sys, R, V, DA, true, false>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (xin) march<Sys, R, V, true, true, true>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else march<Sys, R, V, false, true, true>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      const int y0 = chunk * TY, y1 = min(y0 + TY, g.ny);
+      const bool xin = __all_sync(0xffffffffu, X >= 0 && X + V <= g.nx);
+      if (D < 0) march_async<Sys, R, V, DA, true>(g, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (xin) march<Sys, R, V, true, true, true>(g, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else march<Sys, R, V, false, true, true>(g, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }
-    double l = (double)lam_loc;
+    // the maximum is exact in any precision: reduce in R, widen once
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
+    for (int o = 16; o > 0; o >>= 1) lam_loc = fmax(lam_loc, __shfl_xor_sync(0xffffffffu, lam_loc, o));
+    const double l = (double)lam_loc;
     const int anybad = __any_sync(0xffffffffu, bad != 0u);
     __syncwarp();  // every lane's stores of this task precede lane 0's fence below
     if (lane == 0) {
@@ -172,14 +206,29 @@ fv_batch_kernel(const BatchArgs<R> b) {
         // last task of step s of instance i: close the step
         __threadfence();
         const unsigned e = atomicExch(&ic->err_pending, 0u);
+        Ctrl c;
+        c.step = n;
+        // L2 reads: another SM wrote these fields during this launch
+        c.t = __ldcg(&ic->t);
+        c.t_end = 0.0;
+        c.err_committed = __ldcg(&ic->err_committed);
         if (run) {
-          // L2 reads: another SM wrote these fields during this launch
-          ic->t = __ldcg(&ic->t) + dt;
+          c.t += dt;
+          c.step = n + 1;
+          ic->t = c.t;
           ic->dt_last = dt;
           ic->step = n + 1;
           ic->lam[(n + 2) % 3] = 0ull;
         }
-        if (e) atomicOr(&ic->err_committed, e);
+        if (e) c.err_committed = atomicOr(&ic->err_committed, e) | e;
+        // plan the next step: lmax(W^{n+1}) is complete now
+        StepPlan pl;
+        pl.step = c.step;
+        pl.dt = 0.0;
+        pl.run = choose_dt(a.pol, c, lam_value(__ldcg(&ic->lam[c.step % 3])), &pl.dt, &pl.err) ? 1 : 0;
+        pl.hx = 0.5 * (pl.dt / a.dx);
+        pl.hy = 0.5 * (pl.dt / a.dy);
+        b.plan[i] = pl;
         __threadfence();
         if (i != b.skip_release) st_release(&b.rc[i].released, s + 1);
       }
@@ -203,15 +252,19 @@ struct BatchVariant {
 static const std::vector<BatchVariant> &batch_variants() {
   static std::vector<BatchVariant> out;
   if (out.empty()) {
-    FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, -6, "batch euler f32 v1 ty64 w4 b6 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 4, -6, "batch euler f32 v2 ty64 w4 b4 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 4, -4, "batch euler f32 v2 ty64 w4 b4 async4");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 4, -8, "batch euler f32 v2 ty64 w4 b4 async8");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 32, 4, 4, -6, "batch euler f32 v2 ty32 w4 b4 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 128, 4, 4, -6, "batch euler f32 v2 ty128 w4 b4 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 128, 4, 4, -4, "batch euler f32 v2 ty128 w4 b4 async4");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 128, 4, 5, -6, "batch euler f32 v2 ty128 w4 b5 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 2, 256, 4, 4, -6, "batch euler f32 v2 ty256 w4 b4 async6");
+    FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 5, -6, "batch euler f32 v1 ty64 w4 b5 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, -4, "batch euler f32 v1 ty64 w4 b6 async4");
-    FV_BVARIANT(Euler, kEuler, float, 1, 1, 32, 4, 6, -6, "batch euler f32 v1 ty32 w4 b6 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 5, 0, "batch euler f32 v1 ty64 w4 b5");
-    FV_BVARIANT(Euler, kEuler, float, 1, 1, 128, 4, 5, 0, "batch euler f32 v1 ty128 w4 b5");
-    FV_BVARIANT(Euler, kEuler, float, 1, 2, 64, 4, 3, 0, "batch euler f32 v2 ty64 w4 b3");
     FV_BVARIANT(Euler, kEuler, double, 0, 1, 32, 4, 3, 0, "batch euler f64 v1 ty32 w4 b3");
-    FV_BVARIANT(Euler, kEuler, double, 0, 1, 64, 4, 4, -4, "batch euler f64 v1 ty64 w4 b4 async4");
+    FV_BVARIANT(Euler, kEuler, double, 0, 1, 64, 4, 3, -4, "batch euler f64 v1 ty64 w4 b3 async4");
     FV_BVARIANT(Advection, kAdvection, double, 0, 1, 32, 4, 4, 0, "batch advection f64 v1 ty32 w4 b4");
     FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, 0, "batch advection f32 v1 ty64 w4 b6");
     FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, -6, "batch advection f32 v1 ty64 w4 b6 async6");
@@ -237,6 +290,7 @@ struct fv_batch {
   void *d_args = nullptr;      // StepArgs<R>[n]
   Ctrl *ictrl = nullptr;
   Ctrl *h_ictrl = nullptr;
+  StepPlan *plan = nullptr;    // per-instance dt decision of the next step
   unsigned char *runblock = nullptr;  // RunCounters[n] + ticket + abort
   size_t runblock_bytes = 0;
   unsigned *h_abort = nullptr;
@@ -282,6 +336,7 @@ extern "C" void fv_batch_destroy(fv_batch *b) {
   if (b->arena) cudaFree(b->arena);
   if (b->d_args) cudaFree(b->d_args);
   if (b->ictrl) cudaFree(b->ictrl);
+  if (b->plan) cudaFree(b->plan);
   if (b->h_ictrl) cudaFreeHost(b->h_ictrl);
   if (b->runblock) cudaFree(b->runblock);
   if (b->h_abort) cudaFreeHost(b->h_abort);
@@ -433,6 +488,9 @@ extern "C" fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out)
   if ((e = cudaMalloc(&b->d_args, asz * n)) != cudaSuccess) return bail(e, "args");
   if ((e = cudaMalloc(&b->ictrl, sizeof(Ctrl) * n)) != cudaSuccess) return bail(e, "ctrl");
   if ((e = cudaMemset(b->ictrl, 0, sizeof(Ctrl) * n)) != cudaSuccess) return bail(e, "ctrl");
+  // all-ones: step -1, no plan yet
+  if ((e = cudaMalloc(&b->plan, sizeof(StepPlan) * n)) != cudaSuccess) return bail(e, "plan");
+  if ((e = cudaMemset(b->plan, 0xff, sizeof(StepPlan) * n)) != cudaSuccess) return bail(e, "plan");
   if ((e = cudaMallocHost(&b->h_ictrl, sizeof(Ctrl) * n)) != cudaSuccess) return bail(e, "ctrl");
   b->runblock_bytes = sizeof(RunCounters) * n + 2 * sizeof(unsigned);
   if ((e = cudaMalloc(&b->runblock, b->runblock_bytes)) != cudaSuccess) return bail(e, "counters");
@@ -494,10 +552,11 @@ extern "C" fv_status fv_batch_set_state(fv_batch *b, int k, const void *src, int
     FV_BCUDA(b, cudaMemcpyAsync(b->staging, src, sbytes, cudaMemcpyHostToDevice, b->stream));
     dsrc = b->staging;
   }
-  // the instance restarts at t = 0, step 0
+  // the instance restarts at t = 0, step 0, with no plan
   Ctrl h;
   std::memset(&h, 0, sizeof(h));
   FV_BCUDA(b, cudaMemcpy(b->ictrl + k, &h, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  FV_BCUDA(b, cudaMemset(b->plan + k, 0xff, sizeof(StepPlan)));
   void *buf0 = b->arena + b->off[k];
   FV_BCUDA(b, launch_load_state(b->system, b->prec, dsrc, src_dtype == FV_F32, layout == FV_PRIMITIVE, buf0,
                                 c.nx, c.ny, b->pitch[k], b->plane[k], c.params[0], b->stream));
@@ -522,6 +581,7 @@ static BatchArgs<R> make_batch_args(const fv_batch *b, int nsteps) {
   BatchArgs<R> a;
   a.inst = (const StepArgs<R> *)b->d_args;
   a.ictrl = b->ictrl;
+  a.plan = b->plan;
   a.rc = (RunCounters *)b->runblock;
   a.task_inst = b->task_inst;
   a.task_base = b->task_base;

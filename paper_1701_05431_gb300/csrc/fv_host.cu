@@ -418,7 +418,7 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     if ((e = cudaMemcpy(c->nodes, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(e, "cudaMemcpy(nodes)");
     if ((e = cudaMalloc(&c->lamw, sizeof(double) * 4 * c->plane)) != cudaSuccess) return bail(e, "cudaMalloc(lamw)");
-    c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, c->sms);
+    c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, Q, c->sms);
   }
   int prec = cfg->precision;  // 0 f64, 1 f32, 2 bf16 storage
   int vi = default_variant_for(cfg->system, prec, cfg->nx, cfg->ny, c->sms);

@@ -63,7 +63,7 @@ struct SourceLaunch {
   double K, theta, tol;
   int ug_mode, Q;
 };
-int spray_source_grid(int prec, int sms);
+int spray_source_grid(int prec, int Q, int sms);
 cudaError_t launch_spray_source(const SourceLaunch &L, int grid, cudaStream_t s);
 constexpr int kSprayNodeStride = 9;
 

@@ -12,6 +12,12 @@
 // pre-multiplied weights sit in shared memory.  The multipliers of each cell
 // are kept between steps (warm start): the moments move by O(dt) per step, so
 // Newton usually needs three or four moment evaluations instead of eight.
+// Only the first evaluation of a solve computes the Q exponentials
+// e_q = exp(-p(x_q)) (p the multipliers' polynomial); they stay in shared
+// memory, and after a Newton step d with sum |d_k| <= 2^-10 the next
+// evaluation multiplies them by exp(-p_d(x_q)), |p_d| <= 2^-10, from its
+// Taylor polynomial of degree 6 (truncation < 1e-24 relative), which costs
+// six FMAs instead of an exponential per node.
 // After the update the kernel reduces lmax(W^{n+1}) and closes the step.
 #include <cuda_runtime.h>
 
@@ -41,21 +47,56 @@ template <class R> struct SourceArgs {
 };
 
 // Moments M_k = sum_q w_q 2 x_q x_q^k n(x_q^2), k = 0..6, and
-// M_{-1} = sum_q 2 w_q n(x_q^2) (= m_{-1/2}) of the trial density.
+// M_{-1} = sum_q 2 w_q n(x_q^2) (= m_{-1/2}) of the trial density; the values
+// e_q = n(x_q^2) are left in e[q * es] (es: the thread stride of the cache).
 static __device__ __forceinline__ void me_moments(const double *nd, int Q, const double (&lam)[4],
-                                                  double (&M)[8]) {
+                                                  double (&M)[8], double *e, int es) {
 #pragma unroll
   for (int k = 0; k < 8; ++k) M[k] = 0.0;
   for (int q = 0; q < Q; ++q) {
     const double *r = nd + q * kNodeStride;
     const double x = r[0];
     const double poly = fma(fma(fma(lam[3], x, lam[2]), x, lam[1]), x, lam[0]);
-    const double e = exp(-poly);
+    const double eq = exp(-poly);
+    e[q * es] = eq;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) M[k] = fma(r[1 + k], e, M[k]);
-    M[7] = fma(r[8], e, M[7]);
+    for (int k = 0; k < 7; ++k) M[k] = fma(r[1 + k], eq, M[k]);
+    M[7] = fma(r[8], eq, M[7]);
   }
 }
+
+// exp(-t) for |t| <= 2^-10: Taylor polynomial of degree 6 in Horner form.
+static __device__ __forceinline__ double exp_neg_small(double t) {
+  const double u = -t;
+  double p = 1.0 / 720.0;
+  p = fma(p, u, 1.0 / 120.0);
+  p = fma(p, u, 1.0 / 24.0);
+  p = fma(p, u, 1.0 / 6.0);
+  p = fma(p, u, 0.5);
+  p = fma(p, u, 1.0);
+  return fma(p, u, 1.0);
+}
+
+// The moments after the multipliers moved by d, from the cached e_q of the
+// previous multipliers: e_q <- e_q exp(-(d0 + d1 x + d2 x^2 + d3 x^3)).
+// Requires |d0| + |d1| + |d2| + |d3| <= 2^-10.
+static __device__ __forceinline__ void me_moments_step(const double *nd, int Q, const double (&d)[4],
+                                                       double (&M)[8], double *e, int es) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) M[k] = 0.0;
+  for (int q = 0; q < Q; ++q) {
+    const double *r = nd + q * kNodeStride;
+    const double x = r[0];
+    const double pd = fma(fma(fma(d[3], x, d[2]), x, d[1]), x, d[0]);
+    const double eq = e[q * es] * exp_neg_small(pd);
+    e[q * es] = eq;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) M[k] = fma(r[1 + k], eq, M[k]);
+    M[7] = fma(r[8], eq, M[7]);
+  }
+}
+
+constexpr double kIncrementalStep = 0x1p-10;
 
 // Cholesky solve of the 4 x 4 SPD system H d = r; false if H is not SPD.
 static __device__ __forceinline__ bool spd_solve4(const double (&M)[8], const double (&r)[4],
@@ -102,13 +143,19 @@ static __device__ __forceinline__ bool realizable(const double (&c)[4]) {
          (c[0] - c[1]) * (c[2] - c[3]) - (c[1] - c[2]) * (c[1] - c[2]) > 0.0;
 }
 
-// Maximum-entropy reconstruction: returns false when Newton fails.
+// Maximum-entropy reconstruction: returns false when Newton fails.  e is
+// the thread's exponential cache (Q values, stride es).
 static __device__ bool maxent(const double *nd, int Q, double tol, const double (&m)[4], double (&lam)[4],
-                              double &n0, double &mmh) {
+                              double &n0, double &mmh, double *e, int es) {
   double M[8];
   bool ok = false;
+  // how the moments of the current multipliers are obtained: 0 from scratch,
+  // 1 from the cache and the last full Newton step `d`, 2 already in M
+  int have = 0;
+  double d[4] = {0.0, 0.0, 0.0, 0.0};
   for (int it = 0; it < 100; ++it) {
-    me_moments(nd, Q, lam, M);
+    if (have == 0) me_moments(nd, Q, lam, M, e, es);
+    else if (have == 1) me_moments_step(nd, Q, d, M, e, es);
     double r[4], worst = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -120,7 +167,6 @@ static __device__ bool maxent(const double *nd, int Q, double tol, const double 
       break;
     }
     if (!(worst == worst)) return false;
-    double d[4];
     if (!spd_solve4(M, r, d)) return false;
     if (worst >= 1e-3) {
       // far from the solution: halve the step until the dual
@@ -131,22 +177,25 @@ static __device__ bool maxent(const double *nd, int Q, double tol, const double 
       for (int ls = 0; ls < 60; ++ls) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) trial[k] = lam[k] + alpha * d[k];
-        double Mt[8];
-        me_moments(nd, Q, trial, Mt);
-        const double phi = Mt[0] + trial[0] * m[0] + trial[1] * m[1] + trial[2] * m[2] + trial[3] * m[3];
+        // the last trial evaluated is the one accepted: its moments and
+        // exponentials are those of the new multipliers
+        me_moments(nd, Q, trial, M, e, es);
+        const double phi = M[0] + trial[0] * m[0] + trial[1] * m[1] + trial[2] * m[2] + trial[3] * m[3];
         if (phi <= phi0 + 1e-4 * alpha * slope + 4e-16 * fabs(phi0)) break;
         alpha *= 0.5;
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) lam[k] = trial[k];
+      have = 2;
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) lam[k] += d[k];
+      have = fabs(d[0]) + fabs(d[1]) + fabs(d[2]) + fabs(d[3]) <= kIncrementalStep ? 1 : 0;
     }
   }
   if (!ok) {
     // accept a result that stalled at round-off level
-    me_moments(nd, Q, lam, M);
+    me_moments(nd, Q, lam, M, e, es);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (!(fabs(M[k] - m[k]) <= 1e-10 * m[k])) return false;
@@ -163,6 +212,7 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
   __shared__ int s_bad[kSrcWarps];
   __shared__ StepStart s_st;
   __shared__ double s_nodes[kMaxQ * kNodeStride];
+  extern __shared__ double s_exp[];  // Q x kSrcThreads exponentials, one column per thread
   for (int k = threadIdx.x; k < a.Q * kNodeStride; k += blockDim.x) s_nodes[k] = a.nodes[k];
   if (threadIdx.x == 0) s_st = read_step_start(a.pol, a.ctrl);
   __syncthreads();
@@ -192,7 +242,7 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
         lam[1] = lam[2] = lam[3] = 0.0;
       }
       double n0 = 0.0, mmh = 0.0;
-      if (!cell_bad) cell_bad = !maxent(s_nodes, a.Q, a.tol, m, lam, n0, mmh);
+      if (!cell_bad) cell_bad = !maxent(s_nodes, a.Q, a.tol, m, lam, n0, mmh, s_exp + threadIdx.x, kSrcThreads);
       if (!cell_bad) {
         const double K = a.K;
         const double u = w[4] / w[2], v = w[5] / w[2];
@@ -261,11 +311,15 @@ static SourceArgs<R> make_source_args(const SourceLaunch &L) {
   return a;
 }
 
-int spray_source_grid(int prec, int sms) {
+static size_t source_smem(int Q) { return (size_t)Q * kSrcThreads * sizeof(double); }
+
+int spray_source_grid(int prec, int Q, int sms) {
   int nb = 0;
   const void *k = prec == 0 ? (const void *)&fv_spray_source_kernel<double>
                             : (const void *)&fv_spray_source_kernel<float>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kSrcThreads, 0) != cudaSuccess || nb < 1)
+  const size_t sm = source_smem(Q);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kSrcThreads, sm) != cudaSuccess || nb < 1)
     nb = 1;
   return nb * sms;
 }
@@ -274,12 +328,13 @@ cudaError_t launch_spray_source(const SourceLaunch &L, int grid, cudaStream_t s)
   long long need = ((long long)L.nx * L.ny + kSrcThreads - 1) / kSrcThreads;
   if (need < grid) grid = (int)need;
   if (grid < 1) grid = 1;
+  const size_t sm = source_smem(L.Q);
   if (L.prec == 0) {
     SourceArgs<double> a = make_source_args<double>(L);
-    fv_spray_source_kernel<double><<<grid, kSrcThreads, 0, s>>>(a);
+    fv_spray_source_kernel<double><<<grid, kSrcThreads, sm, s>>>(a);
   } else {
     SourceArgs<float> a = make_source_args<float>(L);
-    fv_spray_source_kernel<float><<<grid, kSrcThreads, 0, s>>>(a);
+    fv_spray_source_kernel<float><<<grid, kSrcThreads, sm, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -49,6 +49,20 @@ template <class S> struct StepArgs {
   typename ParamOf<S>::T bc_state[4][8];
 };
 
+// What the march reads of the launch arguments.  The single-instance kernel
+// passes its StepArgs (constants of the launch); the batched kernel builds
+// this in registers from the instance's arguments in shared memory, keeping
+// the boundary states there (read through the pointer on ghost cells only),
+// because the march's stores into shared memory would otherwise force every
+// field to be reloaded.
+template <class S> struct MarchGeo {
+  Ctrl *ctrl;
+  int nx, ny;
+  long long pitch, plane;
+  int bc[4];
+  const typename ParamOf<S>::T (*bc_state)[8];
+};
+
 // ld: read-only path (state never written during the launch); ldcg: L2-coherent
 // loads for the persistent batched kernel, whose launch also writes the state.
 template <class S, int N> struct VecIO;
@@ -150,30 +164,30 @@ template <int N> struct LaneCols {
   int dir[N];  // Dirichlet side of a ghost cell, -1 otherwise
 };
 
-template <int N, class S>
-static __device__ __forceinline__ LaneCols<N> lane_cols(const StepArgs<S> &a, int X) {
+template <int N, class G>
+static __device__ __forceinline__ LaneCols<N> lane_cols(const G &a, int X) {
   LaneCols<N> L;
 #pragma unroll
   for (int c = 0; c < N; ++c) {
     const int col = X + c;
-    int sc = col, cs = -1;
+    int sc = col, dir = -1;
     if (col < 0) {
-      if (col == -1) cs = kW;
+      if (col == -1 && a.bc[kW] == kDirichlet) dir = kW;
       sc = (col == -1 && a.bc[kW] == kPeriodic) ? a.nx - 1 : 0;
     } else if (col >= a.nx) {
-      if (col == a.nx) cs = kE;
+      if (col == a.nx && a.bc[kE] == kDirichlet) dir = kE;
       sc = (col == a.nx && a.bc[kE] == kPeriodic) ? 0 : a.nx - 1;
     }
     L.col[c] = sc;
-    L.dir[c] = (cs >= 0 && a.bc[cs] == kDirichlet) ? cs : -1;
+    L.dir[c] = dir;
   }
   return L;
 }
 
 // Source row of row j (ghost rows -1 and ny from the boundary condition);
 // returns the Dirichlet side when the ghost row is a prescribed state.
-template <class S>
-static __device__ __forceinline__ int row_src(const StepArgs<S> &a, int j, int &dir) {
+template <class G>
+static __device__ __forceinline__ int row_src(const G &a, int j, int &dir) {
   dir = -1;
   if (j < 0) {
     if (a.bc[kS] == kDirichlet) dir = kS;
@@ -187,8 +201,8 @@ static __device__ __forceinline__ int row_src(const StepArgs<S> &a, int j, int &
 }
 
 // Load the lane's V values (V*K cells) of row j of every variable into W.
-template <int NV, int V, bool XIN, bool CG, class A>
-static __device__ __forceinline__ void load_row(const StepArgs<typename Ops<A>::S> &a,
+template <int NV, int V, bool XIN, bool CG, class A, class G>
+static __device__ __forceinline__ void load_row(const G &a,
                                                 const typename Ops<A>::S *__restrict__ base,
                                                 const LaneCols<V * Ops<A>::K> &L, int j, A (&W)[V][NV]) {
   using S = typename Ops<A>::S;
@@ -269,12 +283,13 @@ template <class A, int V, int NV> struct RowState {
 // Compute part of one row of the march (rows j and j+1 in registers): x-work
 // of row j+1, the y-face between rows j and j+1 evaluated once, update and
 // store of row j (by the writer lanes), and the new state's wave speed.
-template <class Sys, class A, int V, bool XIN, bool FIN>
-static __device__ __forceinline__ void advance_row(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+template <class Sys, class A, int V, bool XIN, bool FIN, class G>
+static __device__ __forceinline__ void advance_row(const G &a, const SysParams<A> &P,
                                                    typename Ops<A>::S *__restrict__ dst_lane, int X, int j,
                                                    bool writer, A lx, A ly, RowState<A, V, Sys::NV> &cur,
                                                    RowState<A, V, Sys::NV> &nxt, A (&Fs)[V][Sys::NV],
-                                                   typename Ops<A>::P &lam_loc, unsigned &bad) {
+                                                   typename Ops<A>::P &lam_loc, unsigned &bad,
+                                                   bool xin = false) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV, K = Ops<A>::K, N = V * K;
   using O = Ops<A>;
@@ -290,9 +305,11 @@ static __device__ __forceinline__ void advance_row(const StepArgs<typename Ops<A
       Fs[c][v] = Fn;
     }
   }
+  // interior strip: XIN at compile time, or xin at run time
+  const bool in = XIN || xin;
   if (writer) {
     S *row = dst_lane + (long long)j * a.pitch;
-    if (XIN || X + N <= a.nx) {
+    if (in || X + N <= a.nx) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         S t[N];
@@ -316,7 +333,7 @@ static __device__ __forceinline__ void advance_row(const StepArgs<typename Ops<A
       for (int c = 0; c < V; ++c) {
         // packed cells inside the grid (all of them on interior strips)
         unsigned valid = (1u << K) - 1u;
-        if (!XIN) {
+        if (!in) {
           valid = 0u;
 #pragma unroll
           for (int k = 0; k < K; ++k)
@@ -333,8 +350,8 @@ static __device__ __forceinline__ void advance_row(const StepArgs<typename Ops<A
 
 // One row of the march with register prefetch: `nxt` receives row j+1
 // (already prefetched in Pf) and Pf is refilled with row j+2.
-template <class Sys, class A, int V, bool XIN, bool FIN, bool CG>
-static __device__ __forceinline__ void march_row(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+template <class Sys, class A, int V, bool XIN, bool FIN, bool CG, class G>
+static __device__ __forceinline__ void march_row(const G &a, const SysParams<A> &P,
                                                  const typename Ops<A>::S *__restrict__ src,
                                                  typename Ops<A>::S *__restrict__ dst_lane,
                                                  const LaneCols<V * Ops<A>::K> &L, int X, int j, int y1,
@@ -353,8 +370,8 @@ static __device__ __forceinline__ void march_row(const StepArgs<typename Ops<A>:
 
 // March one warp task with register prefetch: rows [y0, y1) of the strip
 // whose lane l holds the V*K cells starting at column X.
-template <class Sys, class A, int V, bool XIN, bool FIN, bool CG = false>
-static __device__ __forceinline__ void march(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+template <class Sys, class A, int V, bool XIN, bool FIN, bool CG = false, class G>
+static __device__ __forceinline__ void march(const G &a, const SysParams<A> &P,
                                              const typename Ops<A>::S *__restrict__ src,
                                              typename Ops<A>::S *__restrict__ dst, int X, int y0, int y1,
                                              bool writer, A lx, A ly, typename Ops<A>::P &lam_loc,
@@ -462,8 +479,8 @@ template <class A, int V, int NV, int D> struct RowRing {
 };
 
 // Lane 0 stages row j (relative row r of the task) into slot r % D.
-template <class A, int V, int NV, int D>
-static __device__ __forceinline__ void ring_issue(const StepArgs<typename Ops<A>::S> &a,
+template <class A, int V, int NV, int D, class G>
+static __device__ __forceinline__ void ring_issue(const G &a,
                                                   const typename Ops<A>::S *__restrict__ src,
                                                   RowRing<A, V, NV, D> &rg, int r, int j) {
   using S = typename Ops<A>::S;
@@ -485,8 +502,8 @@ static __device__ __forceinline__ void ring_issue(const StepArgs<typename Ops<A>
 
 // Every lane takes its cells of row j (relative row r) out of its slot,
 // then the slot is refilled with relative row r + D (row j + D) if any.
-template <class A, int V, int NV, int D>
-static __device__ __forceinline__ void ring_fetch(const StepArgs<typename Ops<A>::S> &a,
+template <class A, int V, int NV, int D, class G>
+static __device__ __forceinline__ void ring_fetch(const G &a,
                                                   const typename Ops<A>::S *__restrict__ src,
                                                   RowRing<A, V, NV, D> &rg, int r, int j, int nrows,
                                                   A (&W)[V][NV]) {
@@ -529,8 +546,8 @@ static __device__ __forceinline__ void ring_fetch(const StepArgs<typename Ops<A>
 }
 
 // March one interior warp task through the TMA ring.
-template <class Sys, class A, int V, int D, bool FIN>
-static __device__ __forceinline__ void march_tma(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+template <class Sys, class A, int V, int D, bool FIN, class G>
+static __device__ __forceinline__ void march_tma(const G &a, const SysParams<A> &P,
                                                  const typename Ops<A>::S *__restrict__ src,
                                                  typename Ops<A>::S *__restrict__ dst,
                                                  RowRing<A, V, Sys::NV, D> &rg, int X, int y0, int y1,
@@ -623,15 +640,15 @@ template <class S, int N, int NV, int D> struct LaneRing {
   __device__ __forceinline__ S *slot(int s, int v) const { return buf + ((s * NV + v) * 32) * N; }
 };
 
-// Issue the copies of row j into ring slot r % D.  Interior strips (XIN)
+// Issue the copies of row j into ring slot r % D.  Interior strips (xin)
 // copy each lane's N contiguous cells per variable; strips at the east or
 // west boundary map every cell through lane_cols: a real or ghost column is
 // copied on its own (4 or 8 bytes; 2-byte cells are loaded and stored
 // directly), a Dirichlet ghost value is stored directly.  Direct stores land
 // in the lane's own slots, so program order makes them visible to its reads.
-template <class A, int V, int NV, int D, bool XIN>
-static __device__ __forceinline__ void lring_issue(const StepArgs<typename Ops<A>::S> &a,
-                                                   const typename Ops<A>::S *__restrict__ src, int X,
+template <class A, int V, int NV, int D, class G>
+static __device__ __forceinline__ void lring_issue(const G &a,
+                                                   const typename Ops<A>::S *__restrict__ src, int X, bool xin,
                                                    const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
                                                    int r, int j) {
   using S = typename Ops<A>::S;
@@ -644,7 +661,7 @@ static __device__ __forceinline__ void lring_issue(const StepArgs<typename Ops<A
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = (S)a.bc_state[dir][v];
-  } else if (XIN) {
+  } else if (xin) {
     const S *g = src + X + (long long)sj * a.pitch;
 #pragma unroll
     for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), g + v * a.plane);
@@ -677,18 +694,20 @@ static __device__ __forceinline__ void lring_read(const LaneRing<typename Ops<A>
   }
 }
 
-// March one warp task through the per-lane cp.async ring (XIN: interior
-// strip, every lane's cells inside the grid).  Rows
+// March one warp task through the per-lane cp.async ring (xin: interior
+// strip, every lane's cells inside the grid; one code body serves both kinds
+// of strips, which keeps the instruction footprint small when a launch mixes
+// them).  Rows
 // are numbered r = 0 .. nrows - 1 (row y0 - 1 + r); before reading row r the
 // lane has issued rows up to r + D - 2 and waits until at most D - 2 copy
 // groups are pending, i.e. row r has landed.  A slot is refilled only after
 // the row read from it has been consumed by the flux computation.
-template <class Sys, class A, int V, int D, bool FIN, bool XIN>
-static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A>::S> &a, const SysParams<A> &P,
+template <class Sys, class A, int V, int D, bool FIN, class G>
+static __device__ __forceinline__ void march_async(const G &a, const SysParams<A> &P,
                                                    const typename Ops<A>::S *__restrict__ src,
                                                    typename Ops<A>::S *__restrict__ dst,
                                                    const LaneRing<typename Ops<A>::S, V * Ops<A>::K, Sys::NV, D> &rg,
-                                                   int X, int y0, int y1, bool writer, A lx, A ly,
+                                                   int X, bool xin, int y0, int y1, bool writer, A lx, A ly,
                                                    typename Ops<A>::P &lam_loc, unsigned &bad) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV;
@@ -698,7 +717,7 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
   // prologue: rows 0 .. D-2 in flight (empty groups past the end keep the count)
 #pragma unroll
   for (int r = 0; r < D - 1; ++r) {
-    if (r < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, r, y0 - 1 + r);
+    if (r < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, r, y0 - 1 + r);
     else cp_async_commit();
   }
   RowState<A, V, NV> RA, RB;
@@ -710,12 +729,12 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
     A Fx_[NV], sx_;
     Sys::fluxes(RA.W[c], P, Fx_, sx_, RA.Fy[c], RA.sy[c]);
   }
-  if (D - 1 < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, D - 1, y0 - 1 + D - 1);
+  if (D - 1 < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, D - 1, y0 - 1 + D - 1);
   else cp_async_commit();
   cp_async_wait<D - 2>();
   lring_read<A, V, NV, D>(rg, 1, RB.W);
   row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
-  if (D < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, D, y0 - 1 + D);
+  if (D < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, D, y0 - 1 + D);
   else cp_async_commit();
 #pragma unroll
   for (int c = 0; c < V; ++c) {
@@ -730,8 +749,8 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       lring_read<A, V, NV, D>(rg, r, RA.W);
-      advance_row<Sys, A, V, XIN, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad);
-      if (r + D - 1 < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, r + D - 1, y0 - 1 + r + D - 1);
+      advance_row<Sys, A, V, false, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad, xin);
+      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -740,8 +759,8 @@ static __device__ __forceinline__ void march_async(const StepArgs<typename Ops<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       lring_read<A, V, NV, D>(rg, r, RB.W);
-      advance_row<Sys, A, V, XIN, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad);
-      if (r + D - 1 < nrows) lring_issue<A, V, NV, D, XIN>(a, src, X, rg, r + D - 1, y0 - 1 + r + D - 1);
+      advance_row<Sys, A, V, false, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad, xin);
+      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -819,8 +838,7 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
       // warp-uniform: does every lane of the strip read real columns only?
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
       if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (D < 0 && xin) march_async<Sys, A, V, DA, FIN, true>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (D < 0) march_async<Sys, A, V, DA, FIN, false>(a, P, src, dst, lrg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (D < 0) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);
       else if (xin) march<Sys, A, V, true, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else march<Sys, A, V, false, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }

@@ -3,11 +3,15 @@
   python -m paper_1701_05431_gb300.profile_cases step --system euler --precision f32 --n 4096 --steps 3
   python -m paper_1701_05431_gb300.profile_cases batch --instances 96 --steps 4 --tune 2
   python -m paper_1701_05431_gb300.profile_cases spray --precision f64 --n 1024 --steps 3
+  python -m paper_1701_05431_gb300.profile_cases sweep --workload c3 --precision f32
 
-Each case builds its seeded synthetic input (the `workloads` generators),
-copies it to the device, sets the state through the C ABI and advances the
-given number of time steps once; nothing is timed.  `--tune K` (K >= 2) forces
-kernel candidate K - 2, so that a capture sees a known kernel.
+Each of the first three cases builds its seeded synthetic input (the
+`workloads` generators), copies it to the device, sets the state through the
+C ABI and advances the given number of time steps once; nothing is timed.
+`--tune K` (K >= 2) forces kernel candidate K - 2, so that a capture sees a
+known kernel.  `sweep` times every compiled candidate in turn on one workload
+(c3: Euler 8192^2 smooth periodic; c2: four-quadrant 2048^2; c4: 512 batched
+instances) with CUDA events and prints one JSON line per candidate.
 """
 from __future__ import annotations
 
@@ -58,9 +62,65 @@ def batch_case(instances: int, steps: int, tune: int, precision: str = "f32") ->
         return b.kernel_info()[1]
 
 
+def _timed(fn, reps=3):
+    """Median device time (s) of fn() after one untimed call."""
+    import torch
+    stream = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return sorted(ts)[len(ts) // 2]
+
+
+def sweep(workload: str, precision: str, steps: int) -> None:
+    import json
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1701_05431_gb300 import fvlib
+    stream = torch.cuda.current_stream().cuda_stream
+    if workload == "c4":
+        insts = wl.batched_quadrants(512)
+        ncells = sum(d["nx"] * d["ny"] for _, _, d in insts)
+        k = 0
+        while True:
+            try:
+                b = fvlib.Batch([d for _, _, d in insts], precision, stream=stream, tune=2 + k)
+            except fvlib.FvError:
+                break
+            with b:
+                for i, (_, prim, _) in enumerate(insts):
+                    b.set_state(i, prim, primitive=True)
+                sec = _timed(lambda: b.run(steps), 2)
+                print(json.dumps({"workload": workload, "precision": precision, "kernel": b.kernel_info()[1],
+                                  "cell_updates_per_s": ncells * steps / sec}), flush=True)
+            k += 1
+        return
+    if workload == "c3":
+        prim, d = wl.smooth_periodic(8192, dtype=np.float32)
+    else:
+        prim, d = wl.four_quadrant(2048, npart=8)
+    dev = _device(prim)
+    for k in range(len(fvlib.kernel_candidates("euler", precision))):
+        with fvlib.Solver(d, precision, stream=stream, tune=2 + k) as s:
+            s.set_state(dev, primitive=True)
+            sec = _timed(lambda: s.run(steps))
+            print(json.dumps({"workload": workload, "precision": precision, "kernel": s.kernel_info()[1],
+                              "cell_updates_per_s": d["nx"] * d["ny"] * steps / sec}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["step", "batch", "spray"])
+    ap.add_argument("case", choices=["step", "batch", "spray", "sweep"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4"])
     ap.add_argument("--system", default="euler", choices=["euler", "advection"])
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--n", type=int, default=4096)
@@ -68,6 +128,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--tune", type=int, default=0)
     a = ap.parse_args(argv)
+    if a.case == "sweep":
+        sweep(a.workload, a.precision, a.steps)
+        return
     if a.case == "step":
         k = step_case(a.system, a.precision, a.n, a.steps, a.tune)
     elif a.case == "spray":
