@@ -146,6 +146,26 @@ fv_status fv_run(fv_ctx *ctx, int nsteps, double t_end, double *t_out);
  * memory owned by the caller.  Synchronises the stream. */
 fv_status fv_get_state(fv_ctx *ctx, void *dst, int dst_is_device, int dst_dtype);
 
+/* Asynchronous snapshot of the current state W^n, the counterpart of the
+ * asynchronous output gathering of Sec. 4.3 (the solution is copied out for
+ * writing while the time steps go on).  Queues on the context's stream a
+ * copy of W^n into a device staging buffer owned by the context (converted
+ * to dst_dtype, FV_F64 or FV_F32, in fv_get_state's layout), then, on a side
+ * stream of the context, the copy of that buffer into dst, caller-owned HOST
+ * memory of nVar * nx * ny values.  Returns without waiting; steps queued
+ * afterwards (fv_run, fv_step) run while the host copy is in flight when dst
+ * is pinned (page-locked) memory; with pageable memory the call returns only
+ * after the copy.  dst must stay valid, and must not be read, until
+ * fv_snapshot_wait returns.  A later snapshot waits on the device for the
+ * previous host copy before it refills the staging buffer.
+ * Errors: FV_ERR_INVALID_ARG (NULL dst, bad dtype), FV_ERR_STATE (no state),
+ * FV_ERR_OOM, FV_ERR_CUDA. */
+fv_status fv_snapshot(fv_ctx *ctx, void *dst, int dst_dtype);
+
+/* Blocks until the last fv_snapshot's copy into host memory is complete
+ * (FV_OK at once if none is pending). */
+fv_status fv_snapshot_wait(fv_ctx *ctx);
+
 /* Per-variable totals sum_ij W_v dx dy of the current state (nVar doubles
  * into host memory), FP64 Neumaier-compensated block sums combined in a
  * fixed order (deterministic).  Synchronises the stream. */

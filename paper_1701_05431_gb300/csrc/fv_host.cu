@@ -63,6 +63,12 @@ struct fv_ctx {
   int src_grid = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // graph capture needs a non-legacy stream
+  // asynchronous snapshots: staging buffer, side stream, events
+  void *snap_buf = nullptr;
+  size_t snap_bytes = 0;
+  cudaStream_t snap_stream = nullptr;
+  cudaEvent_t snap_ready = nullptr, snap_done = nullptr;
+  bool snap_pending = false;
   bool has_state = false;
   int variant = -1;
   int grid = 0;
@@ -447,6 +453,13 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
 extern "C" void fv_destroy(fv_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->snap_stream) {
+    cudaStreamSynchronize(c->snap_stream);
+    cudaStreamDestroy(c->snap_stream);
+  }
+  if (c->snap_ready) cudaEventDestroy(c->snap_ready);
+  if (c->snap_done) cudaEventDestroy(c->snap_done);
+  if (c->snap_buf) cudaFree(c->snap_buf);
   free_graphs(c);
   for (int b = 0; b < 2; ++b)
     if (c->buf[b]) cudaFree(c->buf[b]);
@@ -560,6 +573,49 @@ extern "C" fv_status fv_get_state(fv_ctx *c, void *dst, int dst_is_device, int d
                                  c->stream));
   }
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FV_OK;
+}
+
+extern "C" fv_status fv_snapshot(fv_ctx *c, void *dst, int dst_dtype) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!dst) return fail(c, FV_ERR_INVALID_ARG, "dst is NULL");
+  if (dst_dtype != FV_F64 && dst_dtype != FV_F32) return fail(c, FV_ERR_INVALID_ARG, "bad dst_dtype");
+  if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  if (!c->snap_stream) {
+    FV_CUDA(c, cudaStreamCreateWithFlags(&c->snap_stream, cudaStreamNonBlocking));
+    FV_CUDA(c, cudaEventCreateWithFlags(&c->snap_ready, cudaEventDisableTiming));
+    FV_CUDA(c, cudaEventCreateWithFlags(&c->snap_done, cudaEventDisableTiming));
+  }
+  const size_t need = (size_t)c->cfg.nx * c->cfg.ny * c->nvar * (dst_dtype == FV_F64 ? 8 : 4);
+  if (c->snap_bytes < need) {
+    if (c->snap_pending) FV_CUDA(c, cudaEventSynchronize(c->snap_done));
+    c->snap_pending = false;
+    if (c->snap_buf) cudaFree(c->snap_buf);
+    c->snap_buf = nullptr;
+    c->snap_bytes = 0;
+    FV_CUDA(c, cudaMalloc(&c->snap_buf, need));
+    c->snap_bytes = need;
+  }
+  // the previous host copy must be done before the staging buffer is refilled
+  if (c->snap_pending) FV_CUDA(c, cudaStreamWaitEvent(c->stream, c->snap_done, 0));
+  const void *cur = c->buf[c->h_ctrl->step & 1];
+  FV_CUDA(c, launch_store_state(c->cfg.precision, c->nvar, cur, c->snap_buf, dst_dtype == FV_F32, c->cfg.nx,
+                                c->cfg.ny, c->pitch, c->plane, c->stream));
+  FV_CUDA(c, cudaEventRecord(c->snap_ready, c->stream));
+  FV_CUDA(c, cudaStreamWaitEvent(c->snap_stream, c->snap_ready, 0));
+  FV_CUDA(c, cudaMemcpyAsync(dst, c->snap_buf, need, cudaMemcpyDeviceToHost, c->snap_stream));
+  FV_CUDA(c, cudaEventRecord(c->snap_done, c->snap_stream));
+  c->snap_pending = true;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_snapshot_wait(fv_ctx *c) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!c->snap_pending) return FV_OK;
+  FV_CUDA(c, cudaEventSynchronize(c->snap_done));
+  c->snap_pending = false;
   return FV_OK;
 }
 

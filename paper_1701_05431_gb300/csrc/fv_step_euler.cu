@@ -26,6 +26,8 @@ void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT(float, 1, 2, 64, 4, 4, -8, "euler f32 v2 ty64 w4 b4 async8");
   FV_VARIANT(float, 1, 2, 32, 4, 5, -6, "euler f32 v2 ty32 w4 b5 async6");
   FV_VARIANT(float, 1, 2, 16, 4, 5, -6, "euler f32 v2 ty16 w4 b5 async6");
+  FV_VARIANT(float, 1, 4, 64, 4, 3, -4, "euler f32 v4 ty64 w4 b3 async4");
+  FV_VARIANT(float, 1, 4, 64, 4, 2, -6, "euler f32 v4 ty64 w4 b2 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 4, 0, "euler f32 v2 ty64 w4 b4");
   FV_VARIANT(float, 1, 2, 64, 4, 4, 4, "euler f32 v2 ty64 w4 b4 tma4");
   FV_VARIANT(float, 1, 1, 64, 4, 6, 0, "euler f32 v1 ty64 w4 b6");

@@ -7,7 +7,8 @@ and raises if the library is missing: there is no CPU fallback.
 
 Function names follow the ABI: fv_init, fv_set_state, fv_step, fv_run,
 fv_get_state, fv_totals, fv_time, fv_set_time, fv_lambda_max,
-fv_kernel_info, fv_gauss_legendre, fv_destroy, plus the batched fv_batch_*.
+fv_kernel_info, fv_gauss_legendre, fv_snapshot, fv_snapshot_wait, fv_destroy,
+plus the batched fv_batch_*.
 """
 from __future__ import annotations
 
@@ -57,7 +58,8 @@ _lib = None
 
 EXPORTS = ("fv_status_string", "fv_last_error", "fv_init", "fv_destroy", "fv_set_state", "fv_step",
            "fv_run", "fv_get_state", "fv_totals", "fv_time", "fv_set_time", "fv_lambda_max",
-           "fv_kernel_info", "fv_kernel_candidate", "fv_gauss_legendre")
+           "fv_kernel_info", "fv_kernel_candidate", "fv_gauss_legendre", "fv_snapshot",
+           "fv_snapshot_wait")
 
 
 def library_path() -> str:
@@ -87,6 +89,8 @@ def load(build_if_missing: bool = True):
     L.fv_run.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp]
     L.fv_get_state.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
     L.fv_totals.argtypes = [vp, dp]
+    L.fv_snapshot.argtypes = [vp, vp, ctypes.c_int]
+    L.fv_snapshot_wait.argtypes = [vp]
     L.fv_time.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.fv_set_time.argtypes = [vp, ctypes.c_double, ctypes.c_longlong]
     L.fv_lambda_max.argtypes = [vp, dp]
@@ -244,6 +248,19 @@ class Solver:
         import numpy as np
         out = np.empty((self.nvar, self.ny, self.nx), dtype=dtype)
         return self.get_state(out)
+
+    def snapshot(self, dst):
+        """Queue an asynchronous copy of the current state into host memory
+        `dst` (float32/float64, shape (nvar, ny, nx); pinned memory lets later
+        steps overlap the copy).  Do not read dst before snapshot_wait()."""
+        p, dev = _ptr(dst)
+        if dev:
+            raise ValueError("snapshot target must be host memory")
+        _check(self.lib.fv_snapshot(self.ctx, p, _dtype_code(dst)), self.ctx, self.lib)
+        return dst
+
+    def snapshot_wait(self):
+        _check(self.lib.fv_snapshot_wait(self.ctx), self.ctx, self.lib)
 
     def totals(self):
         import numpy as np
