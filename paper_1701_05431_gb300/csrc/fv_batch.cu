@@ -258,7 +258,6 @@ static const std::vector<BatchVariant> &batch_variants() {
     FV_BVARIANT(Euler, kEuler, float, 1, 2, 32, 4, 4, -6, "batch euler f32 v2 ty32 w4 b4 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 2, 128, 4, 4, -6, "batch euler f32 v2 ty128 w4 b4 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 2, 128, 4, 4, -4, "batch euler f32 v2 ty128 w4 b4 async4");
-    FV_BVARIANT(Euler, kEuler, float, 1, 2, 128, 4, 5, -6, "batch euler f32 v2 ty128 w4 b5 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 2, 256, 4, 4, -6, "batch euler f32 v2 ty256 w4 b4 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 5, -6, "batch euler f32 v1 ty64 w4 b5 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, -4, "batch euler f32 v1 ty64 w4 b6 async4");
@@ -413,7 +412,7 @@ static fv_status batch_select(fv_batch *b, int vi) {
   FV_BCUDA(b, cudaMemcpy(b->task_inst, tinst.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
   FV_BCUDA(b, cudaMemcpy(b->task_base, tbase.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice));
   FV_BCUDA(b, cudaMemcpy(b->d_args, args.data(), asz * b->n, cudaMemcpyHostToDevice));
-  if (V.smem > 48 * 1024)
+  if (V.smem > 0)
     FV_BCUDA(b, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
   int nb = 0;
   FV_BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));

@@ -166,7 +166,7 @@ static int default_variant(int system, int prec) {
 // Blocks of a kernel candidate resident per SM (its register target MINB if
 // the occupancy query fails).
 static int resident_blocks(const Variant &V) {
-  if (V.smem > 48 * 1024 &&
+  if (V.smem > 0 &&
       cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem) != cudaSuccess)
     return V.MINB;
   int nb = 0;
@@ -176,31 +176,25 @@ static int resident_blocks(const Variant &V) {
 }
 
 // Default kernel for an nx x ny grid: the first candidate of (system,
-// precision), unless its warp tasks cannot fill the GPU (fewer than two per
-// resident warp).  Then the candidate with the same lane width, warps,
-// register target and staging but shorter tasks: the tallest one that fills
-// the GPU, else the shortest.
+// precision), in the table's order of preference, whose warp tasks fill the
+// GPU (at least two per resident warp); if none does, the one with the most
+// tasks per resident warp.
 static int default_variant_for(int system, int prec, int nx, int ny, int sms) {
-  const int d = default_variant(system, prec);
-  if (d < 0) return d;
   const auto &vs = all_variants();
-  const long long warps = (long long)resident_blocks(vs[d]) * vs[d].NW * sms;
-  auto fills = [&](const Variant &V) {
-    const long long tasks = (long long)((nx + 30 * V.V - 1) / (30 * V.V)) * ((ny + V.TY - 1) / V.TY);
-    return tasks >= 2LL * warps;
-  };
-  if (fills(vs[d])) return d;
-  int pick = d;
+  int best = -1;
+  double best_ratio = -1.0;
   for (size_t k = 0; k < vs.size(); ++k) {
-    const Variant &V = vs[k], &D0 = vs[d];
-    if (V.system != system || V.precision != prec || V.V != D0.V || V.NW != D0.NW || V.MINB != D0.MINB ||
-        V.D != D0.D || V.TY >= D0.TY)
-      continue;
-    const Variant &P = vs[pick];
-    const bool pf = pick != d && fills(P), vf = fills(V);
-    if (pick == d || (vf && (!pf || V.TY > P.TY)) || (!vf && !pf && V.TY < P.TY)) pick = (int)k;
+    const Variant &V = vs[k];
+    if (V.system != system || V.precision != prec) continue;
+    const double tasks = (double)((nx + 30 * V.V - 1) / (30 * V.V)) * (double)((ny + V.TY - 1) / V.TY);
+    const double ratio = tasks / ((double)resident_blocks(V) * V.NW * sms);
+    if (ratio >= 2.0) return (int)k;
+    if (ratio > best_ratio) {
+      best_ratio = ratio;
+      best = (int)k;
+    }
   }
-  return pick;
+  return best;
 }
 
 static std::vector<int> candidates(int system, int prec) {
@@ -219,7 +213,7 @@ static void free_graphs(fv_ctx *c) {
 static fv_status select_variant(fv_ctx *c, int vi) {
   const Variant &V = all_variants()[vi];
   int nb = 0;
-  if (V.smem > 48 * 1024)
+  if (V.smem > 0)
     FV_CUDA(c, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
   FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));
   if (nb < 1) return fail(c, FV_ERR_CUDA, std::string("kernel cannot launch: ") + V.desc);

@@ -20,19 +20,25 @@ void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT(double, 0, 1, 32, 4, 1, 0, "euler f64 v1 ty32 w4");
   FV_VARIANT(double, 0, 1, 16, 4, 1, 0, "euler f64 v1 ty16 w4");
   FV_VARIANT(double, 0, 1, 64, 4, 4, -4, "euler f64 v1 ty64 w4 b4 async4");
+  FV_VARIANT(float, 1, 4, 32, 4, 3, -4, "euler f32 v4 ty32 w4 b3 async4");
+  FV_VARIANT(float, 1, 4, 64, 4, 3, -4, "euler f32 v4 ty64 w4 b3 async4");
+  FV_VARIANT(float, 1, 4, 16, 4, 3, -4, "euler f32 v4 ty16 w4 b3 async4");
+  FV_VARIANT(float, 1, 4, 64, 4, 3, -3, "euler f32 v4 ty64 w4 b3 async3");
+  FV_VARIANT(float, 1, 4, 64, 4, 3, -6, "euler f32 v4 ty64 w4 b3 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 5, -6, "euler f32 v2 ty64 w4 b5 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 4, -6, "euler f32 v2 ty64 w4 b4 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 5, -4, "euler f32 v2 ty64 w4 b5 async4");
   FV_VARIANT(float, 1, 2, 64, 4, 4, -8, "euler f32 v2 ty64 w4 b4 async8");
   FV_VARIANT(float, 1, 2, 32, 4, 5, -6, "euler f32 v2 ty32 w4 b5 async6");
   FV_VARIANT(float, 1, 2, 16, 4, 5, -6, "euler f32 v2 ty16 w4 b5 async6");
-  FV_VARIANT(float, 1, 4, 64, 4, 3, -4, "euler f32 v4 ty64 w4 b3 async4");
-  FV_VARIANT(float, 1, 4, 64, 4, 2, -6, "euler f32 v4 ty64 w4 b2 async6");
   FV_VARIANT(float, 1, 2, 64, 4, 4, 0, "euler f32 v2 ty64 w4 b4");
   FV_VARIANT(float, 1, 2, 64, 4, 4, 4, "euler f32 v2 ty64 w4 b4 tma4");
   FV_VARIANT(float, 1, 1, 64, 4, 6, 0, "euler f32 v1 ty64 w4 b6");
   FV_VARIANT(F2, 1, 1, 64, 4, 4, -6, "euler f32 x2 v1 ty64 w4 b4 async6");
+  FV_VARIANT(BF, 2, 4, 32, 4, 3, -4, "euler bf16 v4 ty32 w4 b3 async4");
+  FV_VARIANT(BF, 2, 4, 64, 4, 3, -4, "euler bf16 v4 ty64 w4 b3 async4");
   FV_VARIANT(BF, 2, 2, 64, 4, 5, -6, "euler bf16 v2 ty64 w4 b5 async6");
+  FV_VARIANT(BF, 2, 2, 16, 4, 5, -6, "euler bf16 v2 ty16 w4 b5 async6");
   FV_VARIANT(BF, 2, 2, 64, 4, 4, -6, "euler bf16 v2 ty64 w4 b4 async6");
   FV_VARIANT(BF, 2, 2, 64, 4, 4, 0, "euler bf16 v2 ty64 w4 b4");
 }

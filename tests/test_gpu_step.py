@@ -215,11 +215,11 @@ def test_constant_state_bitwise(precision, bc):
 
 
 def test_default_kernel_fills_the_gpu_on_small_grids():
-    """Without tuning, a grid whose warp tasks of the first candidate cannot
-    fill the GPU gets the same kernel with shorter tasks; large grids keep
-    the first candidate."""
+    """Without tuning, a large grid gets the first candidate; a grid whose
+    warp tasks cannot fill the GPU with it gets a candidate with shorter
+    tasks."""
     f = fv()
-    for precision in ("f32", "f64"):
+    for precision in ("f32", "f64", "bf16"):
         first = f.kernel_candidates("euler", precision)[0]
         big = wl.problem("euler", 8192, 8192)
         small = wl.problem("euler", 256, 256)
@@ -227,8 +227,7 @@ def test_default_kernel_fills_the_gpu_on_small_grids():
             assert s.kernel_info()[1] == first
         with f.Solver(small, precision) as s:
             got = s.kernel_info()[1]
-        assert got != first and "ty16" in got, got
-        assert got.replace("ty16", "ty64") == first
+        assert got != first and "ty16" in got, (precision, got)
 
 
 def test_periodic_conservation_fp64_and_fp32_drift():
