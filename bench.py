@@ -274,6 +274,52 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
                                      "hbm_frac": nb / sec / 1e9 / hbm, "kernel": b.kernel_info()[1],
                                      "kernel_choice": "autotuned (one timed step per candidate before the first run)",
                                      "launches_per_job": 1}
+    # The paper's fixed dt (per instance: 0.4 min(dx, dy) / lmax(W^0)) on the
+    # same 512 instances, step-gated and with device dataflow (neighbour
+    # dependencies, no barrier per step); and one 8192^2 grid as a batch of one
+    # against the per-step launches of fv_run.
+    def lmax0(prim, gamma=1.4):
+        rho, u, v, p = prim
+        return float(np.max(np.maximum(np.abs(u), np.abs(v)) + np.sqrt(gamma * p / rho)))
+
+    def fixed(prim, dd):
+        return dict(dd, fixed_dt=0.4 * min(1.0 / dd["nx"], 1.0 / dd["ny"]) / lmax0(prim))
+
+    insts = wl.batched_quadrants(512)
+    cfgs = [fixed(pr, dd) for _, pr, dd in insts]
+    for mode in ("gated", "dataflow"):
+        with fvlib.Batch(cfgs, "f32", stream=sptr, tune=1) as b:
+            for k, (_, pr, _) in enumerate(insts):
+                b.set_state(k, pr, primitive=True)
+            b.set_dataflow(mode == "dataflow")
+            sec = timed(lambda: b.run(200), 1)
+            out[f"c4_fixed_dt_{mode}_f32"] = {
+                "cell_updates_per_s": ncells * 200 / sec, "ms_per_job": sec * 1e3,
+                "hbm_frac": 2 * 4 * 4 * ncells * 200 / sec / 1e9 / hbm, "kernel": b.kernel_info()[1]}
+    del insts, cfgs
+    prim, d = wl.smooth_periodic(8192, dtype=np.float32)
+    dfix = fixed(prim, d)
+    pd = torch.from_numpy(prim).to(f"cuda:{local}")
+    with fvlib.Solver(dfix, "f32", stream=sptr) as s:
+        def job():
+            s.set_state(pd, primitive=True)
+            s.run(100)
+        sec = timed(job, 1)
+        out["c3_fixed_dt_per_step_launches_f32"] = {"cell_updates_per_s": 8192 * 8192 * 100 / sec,
+                                                    "ms_per_job": sec * 1e3, "kernel": s.kernel_info()[1],
+                                                    "note": "job = set_state from device + 100 steps"}
+    for mode in ("gated", "dataflow"):
+        with fvlib.Batch([dfix], "f32", stream=sptr, tune=1) as b:
+            b.set_dataflow(mode == "dataflow")
+
+            def job():
+                b.set_state(0, pd, primitive=True)
+                b.run(100)
+            sec = timed(job, 1)
+            out[f"c3_fixed_dt_batch_of_one_{mode}_f32"] = {
+                "cell_updates_per_s": 8192 * 8192 * 100 / sec, "ms_per_job": sec * 1e3,
+                "kernel": b.kernel_info()[1], "note": "job = set_state from device + 100 steps, one launch"}
+    del pd
     # C5: spray moments 2048^2, periodic, 200 steps; FP64 plain and FP32-bulk
     prim, d = wl.spray_field(2048)
     pd = torch.from_numpy(prim).to(f"cuda:{local}")

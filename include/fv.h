@@ -262,6 +262,19 @@ fv_status fv_batch_kernel_info(fv_batch *b, int *variant, const char **desc);
  * run returns FV_ERR_TIMEOUT without touching the GPU's health. */
 fv_status fv_batch_set_wait_limit(fv_batch *b, double seconds, int never_release_instance);
 
+/* Dataflow mode (on != 0): the instances advance with the paper's fixed dt
+ * (Sec. 2.2.1) and, instead of one step-wide barrier per instance, every
+ * warp task of step s waits only for its own and its neighbour tasks' step
+ * s - 1 (the dependencies of the paper's task graph, Sec. 3.2, on the
+ * device).  Results, times, step counts and errors are those of the default
+ * step-gated mode, bit for bit: a task that finds dt lmax > min(dx, dy) on
+ * cells it produced flags its instance, which is then put back to its state
+ * at the start of the run (the library keeps one extra copy of every
+ * instance's state for this) and replayed step-gated.  Requires fixed_dt > 0
+ * for every instance (FV_ERR_INVALID_ARG otherwise); FV_ERR_OOM if the copy
+ * cannot be allocated. */
+fv_status fv_batch_set_dataflow(fv_batch *b, int on);
+
 /* Detail of the last failure on this batch ("" if none). */
 const char *fv_batch_last_error(const fv_batch *b);
 

@@ -17,6 +17,21 @@
 // number of resident blocks.  Every wait is bounded (%globaltimer); on
 // timeout the kernel raises an abort flag, every warp leaves at its next
 // ticket, and the host reports FV_ERR_TIMEOUT.
+//
+// Dataflow mode (the paper's fixed dt, Sec. 2.2.1, with its task graph of
+// Sec. 3.2 on the device).  With a constant dt no step waits for a global
+// lmax: a task of step s only needs its own and its (up to eight) neighbour
+// tasks' step s - 1 to be done, the neighbours being the tasks whose cells
+// its halo reads (across a periodic boundary too).  Every task publishes
+// the number of steps it has completed in this run (release store) and lanes
+// 0..8 of a warp wait on one dependency each (acquire, bounded).  Each task
+// checks the paper's condition dt lmax <= min(dx, dy) on the cells it
+// produced; a violation (or an inadmissible state) flags its instance, whose
+// later tasks then do no work.  Tasks far from the violation may already have
+// advanced past it, so the run keeps a copy of every instance's state at its
+// start: the host puts flagged instances back and replays them with the
+// step-gated kernel, which stops exactly at the failing step, as without
+// dataflow.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,6 +63,14 @@ struct StepPlan {
   unsigned err;
 };
 
+// What one run needs to know per instance (written by the host before it).
+struct RunInfo {
+  long long base;            // step count at the start of the run
+  int active;                // 0: the instance does not advance in this run
+  int pad_;
+  double dt, hx, hy;         // dataflow: the fixed dt and dt / (2 dx), dt / (2 dy)
+};
+
 template <class R> struct BatchArgs {
   const StepArgs<R> *inst;   // per-instance geometry, buffers, dt policy, BCs
   Ctrl *ictrl;               // per-instance lmax slots, t, step, error flags
@@ -60,6 +83,10 @@ template <class R> struct BatchArgs {
   int nsteps, T;
   long long timeout_ns;
   int skip_release;          // instance whose steps are never released (-1: none)
+  int dataflow;              // 1: neighbour dependencies, fixed dt (see the file header)
+  const RunInfo *info;       // per instance
+  unsigned *tdone;           // T entries: steps of this run each task has completed (dataflow)
+  unsigned *flagged;         // per instance: violation seen in this run (dataflow)
 };
 
 static __device__ __forceinline__ unsigned long long global_ns() {
@@ -124,11 +151,7 @@ fv_batch_kernel(const BatchArgs<R> b) {
     const int r = (int)(t - s * (unsigned)b.T);
     const int i = b.task_inst[r];
     const int lt = r - b.task_base[i];
-    int ok = 1;
-    if (lane == 0) ok = wait_at_least(&b.rc[i].released, s, b.timeout_ns, b.abort) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
-    if (!ok) break;
+    if (!__ldg(&b.info[i].active)) continue;  // warp-uniform
     if (i != cur_inst) {
       const unsigned *src = reinterpret_cast<const unsigned *>(&b.inst[i]);
       unsigned *dstw = reinterpret_cast<unsigned *>(&a);
@@ -136,15 +159,40 @@ fv_batch_kernel(const BatchArgs<R> b) {
       __syncwarp();
       cur_inst = i;
     }
+    int ok = 1;
+    if (b.dataflow) {
+      // lanes 0..8 wait on the task itself and its neighbours (dx, dy in -1..1)
+      if (lane < 9 && s > 0u) {
+        int nsx = lt % a.nstrips + lane % 3 - 1, ncy = lt / a.nstrips + lane / 3 - 1;
+        bool dep = true;
+        if (nsx < 0) { if (a.bc[kW] == kPeriodic) nsx += a.nstrips; else dep = false; }
+        if (nsx >= a.nstrips) { if (a.bc[kE] == kPeriodic) nsx -= a.nstrips; else dep = false; }
+        if (ncy < 0) { if (a.bc[kS] == kPeriodic) ncy += a.nchunks; else dep = false; }
+        if (ncy >= a.nchunks) { if (a.bc[kN] == kPeriodic) ncy -= a.nchunks; else dep = false; }
+        if (dep)
+          ok = wait_at_least(&b.tdone[b.task_base[i] + ncy * a.nstrips + nsx], s, b.timeout_ns, b.abort) ? 1 : 0;
+      }
+      ok = __all_sync(0xffffffffu, ok != 0) ? 1 : 0;
+    } else {
+      if (lane == 0) ok = wait_at_least(&b.rc[i].released, s, b.timeout_ns, b.abort) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+    }
+    __syncwarp();
+    if (!ok) break;
     Ctrl *ic = &b.ictrl[i];
     // dt of this step of instance i (same rule as the single-instance kernel):
     // from the plan the previous step's closing warp left, else computed here
     // (the first step of a run)
-    const long long n = __ldcg(&ic->step);
+    const long long n = b.dataflow ? __ldg(&b.info[i].base) + (long long)s : __ldcg(&ic->step);
     double dt = 0.0, hx = 0.0, hy = 0.0;
     unsigned err = 0u;
     bool run;
-    if (__ldcg(&b.plan[i].step) == n) {
+    if (b.dataflow) {
+      run = __ldcg(&b.flagged[i]) == 0u;
+      dt = __ldg(&b.info[i].dt);
+      hx = __ldg(&b.info[i].hx);
+      hy = __ldg(&b.info[i].hy);
+    } else if (__ldcg(&b.plan[i].step) == n) {
       run = __ldcg(&b.plan[i].run) != 0;
       err = __ldcg(&b.plan[i].err);
       dt = __ldcg(&b.plan[i].dt);
@@ -192,6 +240,21 @@ fv_batch_kernel(const BatchArgs<R> b) {
     const double l = (double)lam_loc;
     const int anybad = __any_sync(0xffffffffu, bad != 0u);
     __syncwarp();  // every lane's stores of this task precede lane 0's fence below
+    if (b.dataflow) {
+      if (lane == 0) {
+        if (run) {
+          // the paper's check on the produced cells: dt lmax <= min(dx, dy)
+          if (anybad || !(dt * l <= a.pol.h)) atomicExch(&b.flagged[i], 1u);
+          if (anybad) atomicOr(&ic->err_pending, kErrNonphysical);
+          // lmax of the final state, for the steps after this run
+          if (s + 1u == (unsigned)b.nsteps && !anybad && l > 0.0) atomicMax(&ic->lam[(n + 1) % 3], lam_bits(l));
+        }
+        __threadfence();
+        if (i != b.skip_release) st_release(&b.tdone[r], s + 1u);
+      }
+      __syncwarp();
+      continue;
+    }
     if (lane == 0) {
       if (run) {
         if (anybad) atomicMax(&ic->lam[(n + 1) % 3], 0x7ff8000000000000ull);
@@ -301,6 +364,11 @@ struct fv_batch {
   long long timeout_ns = 2000000000LL;
   int skip_release = -1;
   bool tuned = false;
+  int dataflow = 0;
+  RunInfo *info = nullptr, *h_info = nullptr;  // per instance, device and pinned host
+  char *ckpt = nullptr;                        // dataflow: every instance's state at run start
+  std::vector<size_t> ck_off;
+  size_t tdone_off = 0, flagged_off = 0;       // inside runblock
   void *staging = nullptr;
   size_t staging_bytes = 0;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
@@ -336,6 +404,9 @@ extern "C" void fv_batch_destroy(fv_batch *b) {
   if (b->d_args) cudaFree(b->d_args);
   if (b->ictrl) cudaFree(b->ictrl);
   if (b->plan) cudaFree(b->plan);
+  if (b->info) cudaFree(b->info);
+  if (b->h_info) cudaFreeHost(b->h_info);
+  if (b->ckpt) cudaFree(b->ckpt);
   if (b->h_ictrl) cudaFreeHost(b->h_ictrl);
   if (b->runblock) cudaFree(b->runblock);
   if (b->h_abort) cudaFreeHost(b->h_abort);
@@ -421,6 +492,18 @@ static fv_status batch_select(fv_batch *b, int vi) {
   b->T = T;
   b->variant = vi;
   bfree_graphs(b);
+  // run counters: RunCounters[n], ticket, abort, flagged[n], tdone[T]
+  b->flagged_off = sizeof(RunCounters) * b->n + 2 * sizeof(unsigned);
+  b->tdone_off = b->flagged_off + sizeof(unsigned) * b->n;
+  const size_t rb = b->tdone_off + sizeof(unsigned) * (size_t)T;
+  if (rb != b->runblock_bytes) {
+    if (b->runblock) cudaFree(b->runblock);
+    b->runblock = nullptr;
+    b->runblock_bytes = 0;
+    FV_BCUDA(b, cudaMalloc(&b->runblock, rb));
+    FV_BCUDA(b, cudaMemset(b->runblock, 0, rb));
+    b->runblock_bytes = rb;
+  }
   return FV_OK;
 }
 
@@ -491,9 +574,14 @@ extern "C" fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out)
   if ((e = cudaMalloc(&b->plan, sizeof(StepPlan) * n)) != cudaSuccess) return bail(e, "plan");
   if ((e = cudaMemset(b->plan, 0xff, sizeof(StepPlan) * n)) != cudaSuccess) return bail(e, "plan");
   if ((e = cudaMallocHost(&b->h_ictrl, sizeof(Ctrl) * n)) != cudaSuccess) return bail(e, "ctrl");
-  b->runblock_bytes = sizeof(RunCounters) * n + 2 * sizeof(unsigned);
-  if ((e = cudaMalloc(&b->runblock, b->runblock_bytes)) != cudaSuccess) return bail(e, "counters");
-  if ((e = cudaMemset(b->runblock, 0, b->runblock_bytes)) != cudaSuccess) return bail(e, "counters");
+  if ((e = cudaMalloc(&b->info, sizeof(RunInfo) * n)) != cudaSuccess) return bail(e, "run info");
+  if ((e = cudaMallocHost(&b->h_info, sizeof(RunInfo) * n)) != cudaSuccess) return bail(e, "run info");
+  for (int k = 0; k < n; ++k) {
+    std::memset(&b->h_info[k], 0, sizeof(RunInfo));
+    b->h_info[k].active = 1;
+  }
+  if ((e = cudaMemcpy(b->info, b->h_info, sizeof(RunInfo) * n, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "run info");
   if ((e = cudaMallocHost(&b->h_abort, sizeof(unsigned))) != cudaSuccess) return bail(e, "abort");
   int vi = -1;
   const auto &vs = batch_variants();
@@ -590,11 +678,16 @@ static BatchArgs<R> make_batch_args(const fv_batch *b, int nsteps) {
   a.T = b->T;
   a.timeout_ns = b->timeout_ns;
   a.skip_release = b->skip_release;
+  a.dataflow = b->dataflow;
+  a.info = b->info;
+  a.flagged = (unsigned *)(b->runblock + b->flagged_off);
+  a.tdone = (unsigned *)(b->runblock + b->tdone_off);
   return a;
 }
 
-static fv_status batch_graph(fv_batch *b, int nsteps, cudaGraphExec_t *out) {
-  auto it = b->graphs.find(nsteps);
+static fv_status batch_graph(fv_batch *b, int nsteps, int dataflow, cudaGraphExec_t *out) {
+  const int key = 2 * nsteps + (dataflow ? 1 : 0);
+  auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
     *out = it->second;
     return FV_OK;
@@ -606,10 +699,12 @@ static fv_status batch_graph(fv_batch *b, int nsteps, cudaGraphExec_t *out) {
   if (e == cudaSuccess) {
     if (b->prec == 0) {
       BatchArgs<double> a = make_batch_args<double>(b, nsteps);
+      a.dataflow = dataflow;
       void *args[] = {&a};
       e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, V.smem, b->cap_stream);
     } else {
       BatchArgs<float> a = make_batch_args<float>(b, nsteps);
+      a.dataflow = dataflow;
       void *args[] = {&a};
       e = cudaLaunchKernel(V.kernel, dim3(b->grid), dim3(V.NW * 32), args, V.smem, b->cap_stream);
     }
@@ -625,7 +720,7 @@ static fv_status batch_graph(fv_batch *b, int nsteps, cudaGraphExec_t *out) {
   e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(b, FV_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-  b->graphs[nsteps] = ge;
+  b->graphs[key] = ge;
   *out = ge;
   return FV_OK;
 }
@@ -657,7 +752,7 @@ static fv_status batch_autotune(fv_batch *b) {
   for (int vi : cand) {
     if ((st = batch_select(b, vi)) != FV_OK) break;
     cudaGraphExec_t g;
-    if ((st = batch_graph(b, 1, &g)) != FV_OK) break;
+    if ((st = batch_graph(b, 1, 0, &g)) != FV_OK) break;
     std::vector<float> ms;
     for (int rep = 0; rep < 4 && st == FV_OK; ++rep) {
       if ((st = restore()) != FV_OK) break;
@@ -693,6 +788,99 @@ static fv_status batch_autotune(fv_batch *b) {
   return batch_select(b, best);
 }
 
+// One launch of the persistent kernel for nsteps steps (step-gated or
+// dataflow) and the timeout check; synchronises and refreshes h_ictrl.
+static fv_status batch_launch(fv_batch *b, int nsteps, int dataflow) {
+  cudaGraphExec_t g;
+  fv_status st = batch_graph(b, nsteps, dataflow, &g);
+  if (st != FV_OK) return st;
+  FV_BCUDA(b, cudaGraphLaunch(g, b->stream));
+  FV_BCUDA(b, cudaMemcpyAsync(b->h_abort, b->runblock + sizeof(RunCounters) * b->n + sizeof(unsigned),
+                              sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+  st = read_ictrl(b);
+  if (st != FV_OK) return st;
+  if (*b->h_abort & kErrTimeout) return bfail(b, FV_ERR_TIMEOUT, "a batched-step wait timed out");
+  return FV_OK;
+}
+
+static fv_status upload_info(fv_batch *b) {
+  FV_BCUDA(b, cudaMemcpyAsync(b->info, b->h_info, sizeof(RunInfo) * b->n, cudaMemcpyHostToDevice, b->stream));
+  return FV_OK;
+}
+
+static char *instance_buffer(fv_batch *b, int k, long long step) {
+  return b->arena + b->off[k] + ((step & 1) ? b->bytes[k] : 0);
+}
+
+// Dataflow run (see the file header): instances whose state at the start
+// already fails the paper's check, or that carry a committed error, and the
+// instances flagged during the run, are replayed from their state at the
+// start by the step-gated kernel.
+static fv_status batch_run_dataflow(fv_batch *b, int nsteps) {
+  fv_status st = read_ictrl(b);
+  if (st != FV_OK) return st;
+  const std::vector<Ctrl> saved(b->h_ictrl, b->h_ictrl + b->n);
+  std::vector<int> replay;
+  for (int k = 0; k < b->n; ++k) {
+    const Ctrl &c = saved[k];
+    const double dt = b->cfg[k].fixed_dt, h = b->dx[k] < b->dy[k] ? b->dx[k] : b->dy[k];
+    double lam;
+    std::memcpy(&lam, &c.lam[c.step % 3], sizeof(lam));
+    const bool ok = c.err_committed == 0u && lam <= 1.0e300 && !(dt * lam > h);
+    RunInfo &r = b->h_info[k];
+    r.base = c.step;
+    r.active = ok ? 1 : 0;
+    r.dt = dt;
+    r.hx = 0.5 * (dt / b->dx[k]);
+    r.hy = 0.5 * (dt / b->dy[k]);
+    if (!ok) {
+      replay.push_back(k);
+      continue;
+    }
+    b->h_ictrl[k].lam[(c.step + nsteps) % 3] = 0ull;  // filled by the run's last step
+    FV_BCUDA(b, cudaMemcpyAsync(b->ckpt + b->ck_off[k], instance_buffer(b, k, c.step), b->bytes[k],
+                                cudaMemcpyDeviceToDevice, b->stream));
+  }
+  if ((st = upload_info(b)) != FV_OK) return st;
+  FV_BCUDA(b, cudaMemcpyAsync(b->ictrl, b->h_ictrl, sizeof(Ctrl) * b->n, cudaMemcpyHostToDevice, b->stream));
+  if ((st = batch_launch(b, nsteps, 1)) != FV_OK) return st;
+  std::vector<unsigned> flagged(b->n);
+  FV_BCUDA(b, cudaMemcpy(flagged.data(), b->runblock + b->flagged_off, sizeof(unsigned) * b->n,
+                         cudaMemcpyDeviceToHost));
+  for (int k = 0; k < b->n; ++k) {
+    if (!b->h_info[k].active) continue;
+    Ctrl &c = b->h_ictrl[k];
+    if (flagged[k]) {
+      // back to the state at the start of the run, then replayed below
+      FV_BCUDA(b, cudaMemcpyAsync(instance_buffer(b, k, saved[k].step), b->ckpt + b->ck_off[k], b->bytes[k],
+                                  cudaMemcpyDeviceToDevice, b->stream));
+      c = saved[k];
+      replay.push_back(k);
+      continue;
+    }
+    // what the step-gated kernel's closing warps would have left: t advanced
+    // by the same FP64 additions, the step count, and the lmax slots
+    double t = saved[k].t;
+    for (int j = 0; j < nsteps; ++j) t += b->h_info[k].dt;
+    c.t = t;
+    c.dt_last = b->h_info[k].dt;
+    c.step = saved[k].step + nsteps;
+    c.lam[(c.step + 1) % 3] = 0ull;
+    c.err_pending = 0u;
+    c.blocks_done = 0u;
+  }
+  FV_BCUDA(b, cudaMemcpyAsync(b->ictrl, b->h_ictrl, sizeof(Ctrl) * b->n, cudaMemcpyHostToDevice, b->stream));
+  FV_BCUDA(b, cudaMemsetAsync(b->plan, 0xff, sizeof(StepPlan) * b->n, b->stream));
+  if (!replay.empty()) {
+    for (int k = 0; k < b->n; ++k) b->h_info[k].active = 0;
+    for (int k : replay) b->h_info[k].active = 1;
+    if ((st = upload_info(b)) != FV_OK) return st;
+    if ((st = batch_launch(b, nsteps, 0)) != FV_OK) return st;
+  }
+  FV_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return read_ictrl(b);
+}
+
 extern "C" fv_status fv_batch_run(fv_batch *b, int nsteps) {
   if (!b) return FV_ERR_INVALID_ARG;
   if (nsteps < 0) return bfail(b, FV_ERR_INVALID_ARG, "nsteps < 0");
@@ -706,20 +894,44 @@ extern "C" fv_status fv_batch_run(fv_batch *b, int nsteps) {
     fv_status st = batch_autotune(b);
     if (st != FV_OK) return st;
   }
-  cudaGraphExec_t g;
-  fv_status st = batch_graph(b, nsteps, &g);
+  fv_status st;
+  if (b->dataflow) {
+    st = batch_run_dataflow(b, nsteps);
+    // every instance active again for the runs that follow, whatever happened
+    for (int k = 0; k < b->n; ++k) b->h_info[k].active = 1;
+    fv_status st2 = upload_info(b);
+    if (st2 == FV_OK && cudaStreamSynchronize(b->stream) != cudaSuccess)
+      st2 = bfail(b, FV_ERR_CUDA, "synchronise after a dataflow run");
+    if (st == FV_OK) st = st2;
+  } else {
+    st = batch_launch(b, nsteps, 0);
+  }
   if (st != FV_OK) return st;
-  FV_BCUDA(b, cudaGraphLaunch(g, b->stream));
-  FV_BCUDA(b, cudaMemcpyAsync(b->h_abort, b->runblock + sizeof(RunCounters) * b->n + sizeof(unsigned),
-                              sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
-  st = read_ictrl(b);
-  if (st != FV_OK) return st;
-  if (*b->h_abort & kErrTimeout) return bfail(b, FV_ERR_TIMEOUT, "a batched-step wait timed out");
   unsigned all = 0;
   for (int k = 0; k < b->n; ++k) all |= b->h_ictrl[k].err_committed;
   if (all & kErrCfl) return bfail(b, FV_ERR_CFL, "an instance's fixed dt violates the CFL condition");
   if (all & kErrNonphysical) return bfail(b, FV_ERR_NONPHYSICAL, "an instance reached a non-physical state");
   if (all & kErrZeroSpeed) return bfail(b, FV_ERR_INVALID_ARG, "an instance has lmax = 0");
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_set_dataflow(fv_batch *b, int on) {
+  if (!b) return FV_ERR_INVALID_ARG;
+  if (on) {
+    for (int k = 0; k < b->n; ++k)
+      if (!(b->cfg[k].fixed_dt > 0.0))
+        return bfail(b, FV_ERR_INVALID_ARG, "dataflow needs every instance in fixed-dt mode (fixed_dt > 0)");
+    if (!b->ckpt) {
+      size_t total = 0;
+      b->ck_off.assign(b->n, 0);
+      for (int k = 0; k < b->n; ++k) {
+        b->ck_off[k] = total;
+        total += b->bytes[k];
+      }
+      FV_BCUDA(b, cudaMalloc(&b->ckpt, total));
+    }
+  }
+  b->dataflow = on ? 1 : 0;
   return FV_OK;
 }
 

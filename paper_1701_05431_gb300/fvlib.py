@@ -130,6 +130,8 @@ def _declare_batch(L):
     L.fv_batch_kernel_info.restype = ctypes.c_int
     L.fv_batch_set_wait_limit.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.fv_batch_set_wait_limit.restype = ctypes.c_int
+    L.fv_batch_set_dataflow.argtypes = [vp, ctypes.c_int]
+    L.fv_batch_set_dataflow.restype = ctypes.c_int
 
 
 def make_config(d: dict, precision: str = "f64", stream: int = 0, tune: int = 0) -> fv_config:
@@ -394,6 +396,11 @@ class Batch:
         d = ctypes.c_char_p()
         self._check(self.lib.fv_batch_kernel_info(self.b, ctypes.byref(v), ctypes.byref(d)))
         return v.value, d.value.decode()
+
+    def set_dataflow(self, on: bool = True):
+        """Fixed-dt dataflow mode: neighbour dependencies instead of one
+        barrier per step (same results as the default mode)."""
+        self._check(self.lib.fv_batch_set_dataflow(self.b, 1 if on else 0))
 
     def set_wait_limit(self, seconds: float, never_release_instance: int = -1):
         self._check(self.lib.fv_batch_set_wait_limit(self.b, float(seconds), int(never_release_instance)))

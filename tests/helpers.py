@@ -53,3 +53,16 @@ def transpose_state(W, system):
     elif system == "spray":
         Wt[[4, 5]] = Wt[[5, 4]]
     return Wt
+
+
+def euler_lmax(prim, gamma=1.4):
+    """lmax of a primitive Euler field over the two axis normals:
+    max(|u|, |v|) + sqrt(gamma p / rho)."""
+    rho, u, v, p = prim
+    return float(np.max(np.maximum(np.abs(u), np.abs(v)) + np.sqrt(gamma * p / rho)))
+
+
+def with_fixed_dt(d, prim, cfl):
+    """The problem in the paper's fixed-dt mode, dt = cfl min(dx, dy) / lmax(W^0)."""
+    h = min((d["xmax"] - d["xmin"]) / d["nx"], (d["ymax"] - d["ymin"]) / d["ny"])
+    return dict(d, fixed_dt=cfl * h / euler_lmax(prim))

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from tests.helpers import oracle_problem, rel_l1, rel_linf
+from tests.helpers import oracle_problem, rel_l1, rel_linf, with_fixed_dt
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -137,6 +137,91 @@ def test_batch_wait_timeout_is_reported():
         st = b.run(5, check=False)
         assert st == f.FV_ERR_TIMEOUT
     # the GPU still works
+    _, prim, d = insts[0]
+    W, _ = run_single(d, prim, 3, "f64")
+    assert np.all(np.isfinite(W))
+
+
+# ------------------------------------------------------------------ dataflow
+def run_batch_mode(insts, steps, precision, dataflow, check=True):
+    f = fv()
+    with f.Batch([d for _, _, d in insts], precision) as b:
+        for k, (_, prim, _) in enumerate(insts):
+            b.set_state(k, prim, primitive=True)
+        if dataflow:
+            b.set_dataflow(True)
+        st = b.run(steps, check=check)
+        return st, [b.state(k) for k in range(len(insts))], [b.time(k) for k in range(len(insts))]
+
+
+def fixed_dt_batch(seed=21):
+    """Transmissive four-quadrant instances and periodic smooth ones (whose
+    halos wrap around, so their tasks depend on tasks across the boundary),
+    all in the paper's fixed-dt mode at CFL 0.4."""
+    insts = [(k, prim, with_fixed_dt(d, prim, 0.4)) for k, prim, d in small_batch(5, seed=seed)]
+    for k, (n, m) in enumerate([(97, 61), (150, 33), (31, 200)]):
+        prim, d = wl.random_smooth_euler(n, seed=seed + k, ny=m)
+        insts.append((100 + k, prim, with_fixed_dt(d, prim, 0.4)))
+    return insts
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_dataflow_equals_step_gated_bitwise(precision):
+    """Neighbour dependencies instead of a barrier per step change nothing:
+    states, times and step counts are identical to the step-gated run."""
+    insts = fixed_dt_batch()
+    st0, W0, t0 = run_batch_mode(insts, 37, precision, False)
+    st1, W1, t1 = run_batch_mode(insts, 37, precision, True)
+    assert st0 == st1 == fv().FV_OK
+    for a, b in zip(W1, W0):
+        assert np.array_equal(a, b)
+    assert t1 == t0
+
+
+def test_dataflow_flagged_instance_is_replayed_exactly():
+    """An instance whose Dirichlet inflow has a negative density becomes
+    inadmissible during the run: the dataflow run flags it, puts it back to
+    its state at the start and replays it step-gated, so status, state and
+    step count equal the step-gated run's; the other instances are untouched.
+    A second instance violates the paper's check at its first step (fixed dt
+    above min(dx, dy) / lmax) and never advances, in both modes."""
+    insts = fixed_dt_batch(seed=33)
+    k, prim, d = insts[2]
+    bad = dict(d, bc=("transmissive", "transmissive", "dirichlet", "transmissive"),
+               bc_state=((0,) * 4, (0,) * 4, (-1.0, 0.5, 0.0, 2.0), (0,) * 4))
+    insts[2] = (k, prim, bad)
+    k, prim, d = insts[4]
+    insts[4] = (k, prim, dict(d, fixed_dt=d["fixed_dt"] * 3.0))
+    st0, W0, t0 = run_batch_mode(insts, 25, "f32", False, check=False)
+    st1, W1, t1 = run_batch_mode(insts, 25, "f32", True, check=False)
+    assert st0 == st1 and st0 in (fv().FV_ERR_NONPHYSICAL, fv().FV_ERR_CFL)
+    for a, b in zip(W1, W0):
+        assert np.array_equal(a, b, equal_nan=True)
+    assert t1 == t0
+    assert t0[4][1] == 0 and t0[2][1] < 25 and t0[0][1] == 25
+
+
+def test_dataflow_needs_fixed_dt():
+    f = fv()
+    insts = small_batch(3, seed=2)
+    with f.Batch([d for _, _, d in insts], "f32") as b:
+        with pytest.raises(f.FvError) as e:
+            b.set_dataflow(True)
+        assert e.value.status == f.FV_ERR_INVALID_ARG
+
+
+def test_dataflow_wait_timeout_is_reported():
+    """In dataflow mode too, a dependency that is never released ends the
+    launch with FV_ERR_TIMEOUT after about the limit, and the device stays
+    usable."""
+    f = fv()
+    insts = fixed_dt_batch(seed=44)
+    with f.Batch([d for _, _, d in insts], "f32") as b:
+        for k, (_, prim, _) in enumerate(insts):
+            b.set_state(k, prim, primitive=True)
+        b.set_dataflow(True)
+        b.set_wait_limit(0.2, never_release_instance=1)
+        assert b.run(5, check=False) == f.FV_ERR_TIMEOUT
     _, prim, d = insts[0]
     W, _ = run_single(d, prim, 3, "f64")
     assert np.all(np.isfinite(W))
