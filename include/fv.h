@@ -146,6 +146,19 @@ fv_status fv_run(fv_ctx *ctx, int nsteps, double t_end, double *t_out);
  * memory owned by the caller.  Synchronises the stream. */
 fv_status fv_get_state(fv_ctx *ctx, void *dst, int dst_is_device, int dst_dtype);
 
+/* In-place mode (on != 0; advection and Euler, every precision): the
+ * context keeps ONE state buffer instead of two and updates it in place.
+ * Each warp task writes, besides its cells, its border rows and columns of
+ * W^{n+1} into overlap strips (the paper's ovlpE/N/W/S buffers, Sec. 4.1.2,
+ * here filled by the task that produces the values, not by a copy task);
+ * the next step reads its halo from its neighbours' strips, double-buffered
+ * by step parity, so no task reads a value another is overwriting.  Results
+ * are bit for bit those of the default mode.  Switching frees (on) or
+ * allocates again (off) the second state buffer and keeps the current state,
+ * time and step.  Autotuning (tune = 1) is not done in place.
+ * Errors: FV_ERR_INVALID_ARG (spray system), FV_ERR_OOM, FV_ERR_CUDA. */
+fv_status fv_set_inplace(fv_ctx *ctx, int on);
+
 /* Asynchronous snapshot of the current state W^n, the counterpart of the
  * asynchronous output gathering of Sec. 4.3 (the solution is copied out for
  * writing while the time steps go on).  Queues on the context's stream a

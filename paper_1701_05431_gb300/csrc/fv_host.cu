@@ -49,6 +49,11 @@ struct fv_ctx {
   size_t esize = 0;
   long long pitch = 0, plane = 0;
   size_t buf_bytes = 0;
+  // in-place mode: buf[1] == buf[0], overlap strips of the two parities
+  bool inplace = false;
+  void *ovl = nullptr;
+  size_t ovl_parity_bytes = 0;
+  int ovl_task = 0;
   void *buf[2] = {nullptr, nullptr};
   Ctrl *ctrl = nullptr;
   Ctrl *h_ctrl = nullptr;        // pinned mirror
@@ -159,7 +164,7 @@ static fv_status validate(const fv_config *c) {
 static int default_variant(int system, int prec) {
   const auto &vs = all_variants();
   for (size_t k = 0; k < vs.size(); ++k)
-    if (vs[k].system == system && vs[k].precision == prec) return (int)k;
+    if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace) return (int)k;
   return -1;
 }
 
@@ -179,13 +184,13 @@ static int resident_blocks(const Variant &V) {
 // precision), in the table's order of preference, whose warp tasks fill the
 // GPU (at least two per resident warp); if none does, the one with the most
 // tasks per resident warp.
-static int default_variant_for(int system, int prec, int nx, int ny, int sms) {
+static int default_variant_for(int system, int prec, int nx, int ny, int sms, int inplace = 0) {
   const auto &vs = all_variants();
   int best = -1;
   double best_ratio = -1.0;
   for (size_t k = 0; k < vs.size(); ++k) {
     const Variant &V = vs[k];
-    if (V.system != system || V.precision != prec) continue;
+    if (V.system != system || V.precision != prec || V.inplace != inplace) continue;
     const double tasks = (double)((nx + 30 * V.V - 1) / (30 * V.V)) * (double)((ny + V.TY - 1) / V.TY);
     const double ratio = tasks / ((double)resident_blocks(V) * V.NW * sms);
     if (ratio >= 2.0) return (int)k;
@@ -201,7 +206,7 @@ static std::vector<int> candidates(int system, int prec) {
   std::vector<int> out;
   const auto &vs = all_variants();
   for (size_t k = 0; k < vs.size(); ++k)
-    if (vs[k].system == system && vs[k].precision == prec) out.push_back((int)k);
+    if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace) out.push_back((int)k);
   return out;
 }
 
@@ -236,6 +241,11 @@ static StepArgs<R> make_args(const fv_ctx *c, const Variant &V) {
   std::memset(&a, 0, sizeof(a));
   a.buf0 = (R *)c->buf[0];
   a.buf1 = (R *)c->buf[1];
+  if (c->inplace) {
+    a.ovl[0] = (R *)c->ovl;
+    a.ovl[1] = (R *)((char *)c->ovl + c->ovl_parity_bytes);
+    a.ovl_task = c->ovl_task;
+  }
   a.ctrl = c->ctrl;
   a.nx = c->cfg.nx;
   a.ny = c->cfg.ny;
@@ -456,7 +466,8 @@ extern "C" void fv_destroy(fv_ctx *c) {
   if (c->snap_buf) cudaFree(c->snap_buf);
   free_graphs(c);
   for (int b = 0; b < 2; ++b)
-    if (c->buf[b]) cudaFree(c->buf[b]);
+    if (c->buf[b] && (b == 0 || c->buf[1] != c->buf[0])) cudaFree(c->buf[b]);
+  if (c->ovl) cudaFree(c->ovl);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_scalar) cudaFreeHost(c->h_scalar);
@@ -484,6 +495,33 @@ static fv_status ensure_staging(fv_ctx *c, size_t bytes) {
 
 // Recompute lmax of the current state into slot `step % 3`, clear the other
 // slots and report an inadmissible state.
+// In-place mode: overlap strips of parity step % 2 from the state.
+static fv_status fill_ovl(fv_ctx *c, long long step) {
+  const Variant &V = all_variants()[c->variant];
+  const int sw = 30 * V.V;
+  const int nstrips = (c->cfg.nx + sw - 1) / sw, nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
+  void *dst = (char *)c->ovl + ((step & 1) ? c->ovl_parity_bytes : 0);
+  const long long total = (long long)nstrips * nchunks * c->nvar * (2 * V.TY + 2 * sw);
+  const int th = 256;
+  const int g = (int)std::min<long long>((total + th - 1) / th, 4LL * c->sms * 8);
+  const int p = c->cfg.precision;
+  if (p == 0)
+    fill_ovl_kernel<double><<<g, th, 0, c->stream>>>((const double *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
+                                                     c->plane, c->nvar, nstrips, nchunks, V.TY, sw, c->ovl_task,
+                                                     (double *)dst);
+  else if (p == 1)
+    fill_ovl_kernel<float><<<g, th, 0, c->stream>>>((const float *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
+                                                    c->plane, c->nvar, nstrips, nchunks, V.TY, sw, c->ovl_task,
+                                                    (float *)dst);
+  else
+    fill_ovl_kernel<__nv_bfloat16><<<g, th, 0, c->stream>>>((const __nv_bfloat16 *)c->buf[0], c->cfg.nx, c->cfg.ny,
+                                                            c->pitch, c->plane, c->nvar, nstrips, nchunks, V.TY,
+                                                            sw, c->ovl_task, (__nv_bfloat16 *)dst);
+  FV_CUDA(c, cudaGetLastError());
+  FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return FV_OK;
+}
+
 static fv_status seed(fv_ctx *c, long long step, double t) {
   Ctrl h;
   std::memset(&h, 0, sizeof(h));
@@ -510,6 +548,7 @@ static fv_status seed(fv_ctx *c, long long step, double t) {
     return fail(c, FV_ERR_NONPHYSICAL, "state has rho <= 0, p <= 0, non-finite or non-realizable values");
   }
   c->has_state = true;
+  if (c->inplace) return fill_ovl(c, step);
   return FV_OK;
 }
 
@@ -666,7 +705,8 @@ extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) 
   if (nsteps < 0) return fail(c, FV_ERR_INVALID_ARG, "nsteps < 0");
   if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
   if (!std::isfinite(t_end)) return fail(c, FV_ERR_INVALID_ARG, "t_end must be finite");
-  if (c->cfg.tune == 1 && !c->tuned && nsteps > 0) {
+  // (a trial step would overwrite the state in place: no tuning there)
+  if (c->cfg.tune == 1 && !c->tuned && nsteps > 0 && !c->inplace) {
     fv_status st = autotune(c);
     if (st != FV_OK) return st;
   }
@@ -733,7 +773,7 @@ extern "C" fv_status fv_set_time(fv_ctx *c, double t, long long step) {
   fv_status st = read_ctrl(c);
   if (st != FV_OK) return st;
   const long long cur = c->h_ctrl->step;
-  if ((cur & 1) != (step & 1)) {
+  if ((cur & 1) != (step & 1) && c->buf[0] != c->buf[1]) {
     // the state lives in buffer step % 2: move it to the new parity
     FV_CUDA(c, cudaMemcpyAsync(c->buf[step & 1], c->buf[cur & 1], c->buf_bytes, cudaMemcpyDeviceToDevice,
                                c->stream));
@@ -799,6 +839,59 @@ extern "C" fv_status fv_gauss_legendre(int Q, double *x, double *w) {
     w[Q - 1 - i] = 1.0 / ((1.0 - t * t) * d * d);
   }
   return FV_OK;
+}
+
+extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  on = on ? 1 : 0;
+  if (on == (int)c->inplace) return FV_OK;
+  if (c->cfg.system == FV_SPRAY) return fail(c, FV_ERR_INVALID_ARG, "in-place mode: advection and Euler only");
+  long long step = 0;
+  if (c->has_state) {
+    fv_status st = read_ctrl(c);
+    if (st != FV_OK) return st;
+    step = c->h_ctrl->step;
+  }
+  FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (on) {
+    const int vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 1);
+    if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "no in-place kernel for this system and precision");
+    const Variant &V = all_variants()[vi];
+    const int sw = 30 * V.V;
+    const long long ntasks = (long long)((c->cfg.nx + sw - 1) / sw) * ((c->cfg.ny + V.TY - 1) / V.TY);
+    const int q = (int)(16 / c->esize);  // keep every task's strips 16-byte aligned
+    const int ts = (c->nvar * (2 * V.TY + 2 * sw) + q - 1) / q * q;
+    const size_t pb = ((size_t)ntasks * ts * c->esize + 255) / 256 * 256;
+    void *ovl = nullptr;
+    cudaError_t e = cudaMalloc(&ovl, 2 * pb);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(overlap strips)");
+    if (c->has_state && (step & 1))
+      FV_CUDA(c, cudaMemcpyAsync(c->buf[0], c->buf[1], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    FV_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->buf[1]);
+    c->buf[1] = c->buf[0];
+    c->ovl = ovl;
+    c->ovl_parity_bytes = pb;
+    c->ovl_task = ts;
+    c->inplace = true;
+    fv_status st = select_variant(c, vi);
+    if (st != FV_OK) return st;
+    if (c->has_state) return fill_ovl(c, step);
+    return FV_OK;
+  }
+  void *b1 = nullptr;
+  cudaError_t e = cudaMalloc(&b1, c->buf_bytes);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(state)");
+  if (c->has_state && (step & 1))
+    FV_CUDA(c, cudaMemcpyAsync(b1, c->buf[0], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+  FV_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->buf[1] = b1;
+  cudaFree(c->ovl);
+  c->ovl = nullptr;
+  c->ovl_parity_bytes = 0;
+  c->ovl_task = 0;
+  c->inplace = false;
+  return select_variant(c, default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms));
 }
 
 extern "C" fv_status fv_kernel_candidate(int system, int precision, int index, const char **desc) {

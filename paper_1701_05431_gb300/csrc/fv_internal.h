@@ -23,6 +23,7 @@ struct Variant {
   int smem;        // dynamic shared memory per block (bytes)
   const void *kernel;
   const char *desc;
+  int inplace;     // 1: in-place kernel (one state buffer plus overlap strips)
 };
 
 // Registration hooks, one per translation unit of step kernels.

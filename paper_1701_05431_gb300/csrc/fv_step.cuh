@@ -47,6 +47,10 @@ template <class S> struct StepArgs {
   SysParams<typename ParamOf<S>::T> sp;
   int bc[4];
   typename ParamOf<S>::T bc_state[4][8];
+  // in-place mode: the overlap strips of the two step parities (null in the
+  // default ping-pong mode, where buf0 != buf1)
+  S *ovl[2];
+  int ovl_task;      // elements of one task's strips in one parity
 };
 
 // What the march reads of the launch arguments.  The single-instance kernel
@@ -272,6 +276,136 @@ static __device__ __forceinline__ void row_x(const SysParams<A> &P, const A (&W)
   }
 }
 
+// ---------------------------------------------------------------- in place
+// In-place mode keeps ONE state buffer.  A task updates its own cells in
+// place; the cells of its halo that belong to other tasks are read from the
+// overlap strips those tasks wrote one step earlier (the paper's ovlpE/N/W/S
+// buffers, Sec. 4.1.2, filled by the producing task instead of a copy task):
+// per task and step parity, its west and east border columns (TY values each)
+// and its south and north border rows (30 N values each), for every
+// variable.  Step n reads the strips of parity n % 2 and writes those of
+// parity (n + 1) % 2, so no task reads a value another task is overwriting.
+// A task's own rows are read (through the ring, several rows ahead) before it
+// overwrites them.
+template <class S> struct Ovl {
+  const S *rd;     // strips of parity n % 2 (borders of W^n)
+  S *wr;           // strips of parity (n + 1) % 2 (borders of W^{n+1})
+  int sx, cy;      // this task's strip and chunk
+  int nstrips, nchunks;
+  int X0, y0, y1;  // first column, first and end row of the task
+  int ty, ts;      // rows per task, elements per task in one parity
+};
+
+// Element offsets inside one task's strips (NV variables each).
+template <int NV, int SW> struct OvlLayout {
+  static __device__ __forceinline__ int colW(int ty) { return 0; }
+  static __device__ __forceinline__ int colE(int ty) { return NV * ty; }
+  static __device__ __forceinline__ int rowS(int ty) { return 2 * NV * ty; }
+  static __device__ __forceinline__ int rowN(int ty) { return 2 * NV * ty + NV * SW; }
+};
+
+// Where cell (j, col) of a task's halo-extended tile comes from in place:
+// a Dirichlet side (dir >= 0), or an address p of variable 0 with variable
+// stride vs (the state itself for the task's own cells and for transmissive
+// ghosts, which copy the task's own border, else a neighbour's strip).
+// Cells no face of the task uses (tile corners, idle cells of the halo
+// lanes) resolve to some valid finite value.
+template <int NV, int SW, class G, class S>
+static __device__ __forceinline__ const S *inplace_cell(const G &a, const S *W, const Ovl<S> &o, int j, int col,
+                                                        long long &vs, int &dir, int &kind) {
+  using L = OvlLayout<NV, SW>;
+  dir = -1;
+  kind = 1;  // a row strip, unless changed below
+  const int last = min(o.X0 + SW, a.nx) - 1;  // last real column of the task
+  const int cc = min(max(col, o.X0), last) - o.X0;
+  if (j < o.y0) {
+    if (j < 0) {
+      if (a.bc[kS] == kDirichlet) { dir = kS; return nullptr; }
+      if (a.bc[kS] == kPeriodic) {
+        vs = SW;
+        return o.rd + (long long)((o.nchunks - 1) * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + cc;
+      }
+      j = 0;  // transmissive: the task's own first row
+    } else {
+      vs = SW;
+      return o.rd + (long long)((o.cy - 1) * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + cc;
+    }
+  } else if (j >= o.y1) {
+    if (j >= a.ny) {
+      if (a.bc[kN] == kDirichlet) { dir = kN; return nullptr; }
+      if (a.bc[kN] == kPeriodic) {
+        vs = SW;
+        return o.rd + (long long)o.sx * o.ts + L::rowS(o.ty) + cc;
+      }
+      j = a.ny - 1;  // transmissive: the task's own last row
+    } else {
+      vs = SW;
+      return o.rd + (long long)((o.cy + 1) * o.nstrips + o.sx) * o.ts + L::rowS(o.ty) + cc;
+    }
+  }
+  const int jr = j - o.y0;
+  kind = 2;  // a column strip, unless the cell is the state's
+  if (col < o.X0) {
+    if (o.X0 == 0) {
+      if (a.bc[kW] == kDirichlet) { dir = kW; return nullptr; }
+      if (a.bc[kW] == kPeriodic) {
+        vs = o.ty;
+        return o.rd + (long long)(o.cy * o.nstrips + o.nstrips - 1) * o.ts + L::colE(o.ty) + jr;
+      }
+      col = 0;  // transmissive: the task's own first column
+    } else {
+      vs = o.ty;
+      return o.rd + (long long)(o.cy * o.nstrips + o.sx - 1) * o.ts + L::colE(o.ty) + jr;
+    }
+  } else if (col > last) {
+    if (last == a.nx - 1) {
+      if (a.bc[kE] == kDirichlet) { dir = kE; return nullptr; }
+      if (a.bc[kE] == kPeriodic) {
+        vs = o.ty;
+        return o.rd + (long long)(o.cy * o.nstrips) * o.ts + L::colW(o.ty) + jr;
+      }
+      col = a.nx - 1;  // transmissive: the task's own last column
+    } else {
+      vs = o.ty;
+      return o.rd + (long long)(o.cy * o.nstrips + o.sx + 1) * o.ts + L::colW(o.ty) + jr;
+    }
+  }
+  kind = 0;
+  vs = a.plane;
+  return W + (long long)j * a.pitch + col;
+}
+
+// In-place mode: the writer lanes' share of the task's new border strips
+// (row y0 -> south row strip, row y1 - 1 -> north row strip, first and last
+// real column -> west and east column strips), values of W^{n+1} in storage
+// type, t[v][c] for the lane's N cells.
+template <int NV, int N, class G, class S>
+static __device__ __forceinline__ void write_strips(const G &a, const Ovl<S> &o, int X, int j, const S (&t)[NV][N]) {
+  constexpr int SW = 30 * N;
+  using L = OvlLayout<NV, SW>;
+  S *base = o.wr + (long long)(o.cy * o.nstrips + o.sx) * o.ts;
+  const int last = min(o.X0 + SW, a.nx) - 1;
+  if (j == o.y0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(base + L::rowS(o.ty) + v * SW + (X - o.X0), t[v]);
+  }
+  if (j == o.y1 - 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(base + L::rowN(o.ty) + v * SW + (X - o.X0), t[v]);
+  }
+  const int jr = j - o.y0;
+  if (X == o.X0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) base[L::colW(o.ty) + v * o.ty + jr] = t[v][0];
+  }
+#pragma unroll
+  for (int c = 0; c < N; ++c)
+    if (X + c == last) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) base[L::colE(o.ty) + v * o.ty + jr] = t[v][c];
+    }
+}
+
 // Registers of one row of the march.
 template <class A, int V, int NV> struct RowState {
   A W[V][NV];
@@ -283,13 +417,14 @@ template <class A, int V, int NV> struct RowState {
 // Compute part of one row of the march (rows j and j+1 in registers): x-work
 // of row j+1, the y-face between rows j and j+1 evaluated once, update and
 // store of row j (by the writer lanes), and the new state's wave speed.
-template <class Sys, class A, int V, bool XIN, bool FIN, class G>
+template <class Sys, class A, int V, bool XIN, bool FIN, bool INPL = false, class G>
 static __device__ __forceinline__ void advance_row(const G &a, const SysParams<A> &P,
-                                                   typename Ops<A>::S *__restrict__ dst_lane, int X, int j,
+                                                   typename Ops<A>::S *dst_lane, int X, int j,
                                                    bool writer, A lx, A ly, RowState<A, V, Sys::NV> &cur,
                                                    RowState<A, V, Sys::NV> &nxt, A (&Fs)[V][Sys::NV],
                                                    typename Ops<A>::P &lam_loc, unsigned &bad,
-                                                   bool xin = false) {
+                                                   bool xin = false,
+                                                   const Ovl<typename Ops<A>::S> *ovl = nullptr) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV, K = Ops<A>::K, N = V * K;
   using O = Ops<A>;
@@ -309,25 +444,22 @@ static __device__ __forceinline__ void advance_row(const G &a, const SysParams<A
   const bool in = XIN || xin;
   if (writer) {
     S *row = dst_lane + (long long)j * a.pitch;
+    S t[NV][N];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < V; ++c) O::unpack(Wn[c][v], t[v] + c * K);
     if (in || X + N <= a.nx) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        S t[N];
-#pragma unroll
-        for (int c = 0; c < V; ++c) O::unpack(Wn[c][v], t + c * K);
-        VecIO<S, N>::st(row + v * a.plane, t);
-      }
+      for (int v = 0; v < NV; ++v) VecIO<S, N>::st(row + v * a.plane, t[v]);
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        S t[N];
-#pragma unroll
-        for (int c = 0; c < V; ++c) O::unpack(Wn[c][v], t + c * K);
+      for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int c = 0; c < N; ++c)
-          if (X + c < a.nx) __stcs(row + v * a.plane + c, t[c]);
-      }
+          if (X + c < a.nx) __stcs(row + v * a.plane + c, t[v][c]);
     }
+    if (INPL) write_strips<NV, N>(a, *ovl, X, j, t);
     if (FIN) {
 #pragma unroll
       for (int c = 0; c < V; ++c) {
@@ -681,6 +813,44 @@ static __device__ __forceinline__ void lring_issue(const G &a,
   cp_async_commit();
 }
 
+// In-place counterpart of lring_issue: own rows of lanes 1..30 (all cells in
+// the grid) are one vector copy per variable from the state, halo rows of
+// those lanes one vector copy per variable from the neighbour's row strip;
+// everything else goes cell by cell through inplace_cell.
+template <class A, int V, int NV, int D, class G>
+static __device__ __forceinline__ void lring_issue_inplace(const G &a, const typename Ops<A>::S *W, int X,
+                                                           const Ovl<typename Ops<A>::S> &o,
+                                                           const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
+                                                           int r, int j) {
+  using S = typename Ops<A>::S;
+  constexpr int N = V * Ops<A>::K, SW = 30 * N;
+  const int slot = r % D;
+  const int lane = threadIdx.x & 31;
+  const bool vec = lane >= 1 && lane <= 30 && X + N <= a.nx;
+  long long vs;
+  int dir, kind;
+  // with all N cells in the grid, cell X's source tells where the whole
+  // vector is: a row of the state or of a neighbour's row strip
+  const S *p = inplace_cell<NV, SW>(a, W, o, j, X, vs, dir, kind);
+  if (vec && dir < 0 && kind != 2) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * vs);
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      const S *q = inplace_cell<NV, SW>(a, W, o, j, X + c, vs, dir, kind);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        S *d = rg.slot(slot, v) + c;
+        if (dir >= 0) *d = (S)a.bc_state[dir][v];
+        else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, q + v * vs);
+        else *d = __ldcg(q + v * vs);
+      }
+    }
+  }
+  cp_async_commit();
+}
+
 template <class A, int V, int NV, int D>
 static __device__ __forceinline__ void lring_read(const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
                                                   int r, A (&W)[V][NV]) {
@@ -702,22 +872,27 @@ static __device__ __forceinline__ void lring_read(const LaneRing<typename Ops<A>
 // lane has issued rows up to r + D - 2 and waits until at most D - 2 copy
 // groups are pending, i.e. row r has landed.  A slot is refilled only after
 // the row read from it has been consumed by the flux computation.
-template <class Sys, class A, int V, int D, bool FIN, class G>
+template <class Sys, class A, int V, int D, bool FIN, bool INPL = false, class G>
 static __device__ __forceinline__ void march_async(const G &a, const SysParams<A> &P,
-                                                   const typename Ops<A>::S *__restrict__ src,
-                                                   typename Ops<A>::S *__restrict__ dst,
+                                                   const typename Ops<A>::S *src,
+                                                   typename Ops<A>::S *dst,
                                                    const LaneRing<typename Ops<A>::S, V * Ops<A>::K, Sys::NV, D> &rg,
                                                    int X, bool xin, int y0, int y1, bool writer, A lx, A ly,
-                                                   typename Ops<A>::P &lam_loc, unsigned &bad) {
+                                                   typename Ops<A>::P &lam_loc, unsigned &bad,
+                                                   const Ovl<typename Ops<A>::S> *ovl = nullptr) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV;
   using O = Ops<A>;
   S *dst_lane = dst + X;
   const int nrows = y1 - y0 + 2;
+  auto issue = [&](int r, int j) {
+    if (INPL) lring_issue_inplace<A, V, NV, D>(a, src, X, *ovl, rg, r, j);
+    else lring_issue<A, V, NV, D>(a, src, X, xin, rg, r, j);
+  };
   // prologue: rows 0 .. D-2 in flight (empty groups past the end keep the count)
 #pragma unroll
   for (int r = 0; r < D - 1; ++r) {
-    if (r < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, r, y0 - 1 + r);
+    if (r < nrows) issue(r, y0 - 1 + r);
     else cp_async_commit();
   }
   RowState<A, V, NV> RA, RB;
@@ -729,12 +904,12 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
     A Fx_[NV], sx_;
     Sys::fluxes(RA.W[c], P, Fx_, sx_, RA.Fy[c], RA.sy[c]);
   }
-  if (D - 1 < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, D - 1, y0 - 1 + D - 1);
+  if (D - 1 < nrows) issue(D - 1, y0 - 1 + D - 1);
   else cp_async_commit();
   cp_async_wait<D - 2>();
   lring_read<A, V, NV, D>(rg, 1, RB.W);
   row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
-  if (D < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, D, y0 - 1 + D);
+  if (D < nrows) issue(D, y0 - 1 + D);
   else cp_async_commit();
 #pragma unroll
   for (int c = 0; c < V; ++c) {
@@ -749,8 +924,8 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       lring_read<A, V, NV, D>(rg, r, RA.W);
-      advance_row<Sys, A, V, false, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad, xin);
-      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, r + D - 1, y0 - 1 + r + D - 1);
+      advance_row<Sys, A, V, false, FIN, INPL>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad, xin, ovl);
+      if (r + D - 1 < nrows) issue(r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -759,8 +934,8 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       lring_read<A, V, NV, D>(rg, r, RB.W);
-      advance_row<Sys, A, V, false, FIN>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad, xin);
-      if (r + D - 1 < nrows) lring_issue<A, V, NV, D>(a, src, X, xin, rg, r + D - 1, y0 - 1 + r + D - 1);
+      advance_row<Sys, A, V, false, FIN, INPL>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad, xin, ovl);
+      if (r + D - 1 < nrows) issue(r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
     ++j;
@@ -784,7 +959,7 @@ constexpr __host__ __device__ int async_smem_bytes(int NW) {
 // FIN: this launch also reduces lmax(W^{n+1}) and closes the step (every
 // system but spray, whose source kernel closes the step instead); MINB: blocks
 // per SM the register budget targets; D: row staging (see the file header).
-template <class Sys, class A, int V, int TY, int NW, bool FIN = true, int MINB = 1, int D = 0>
+template <class Sys, class A, int V, int TY, int NW, bool FIN = true, int MINB = 1, int D = 0, bool INPL = false>
 __global__ void __launch_bounds__(NW * 32, MINB)
 fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
   using S = typename Ops<A>::S;
@@ -820,8 +995,9 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
 
   if (st.run) {
     const long long n = st.step;
-    const S *__restrict__ src = (n & 1) ? a.buf1 : a.buf0;
-    S *__restrict__ dst = (n & 1) ? a.buf0 : a.buf1;
+    // in place: buf0 == buf1, so src == dst
+    const S *src = (n & 1) ? a.buf1 : a.buf0;
+    S *dst = (n & 1) ? a.buf0 : a.buf1;
     const SysParams<A> P = splat_params<A>(a.sp);
     // half steps: the face fluxes are carried doubled (see lf_face2)
     const A lx = Ops<A>::splat((typename Ops<A>::P)(0.5 * (st.dt / a.dx)));
@@ -838,7 +1014,21 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
       // warp-uniform: does every lane of the strip read real columns only?
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
       if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (D < 0) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);
+      else if (D < 0 && INPL) {
+        Ovl<S> o;
+        o.rd = a.ovl[n & 1];
+        o.wr = a.ovl[(n + 1) & 1];
+        o.sx = sx_;
+        o.cy = cy;
+        o.nstrips = a.nstrips;
+        o.nchunks = a.nchunks;
+        o.X0 = sx_ * (30 * N);
+        o.y0 = y0;
+        o.y1 = y1;
+        o.ty = TY;
+        o.ts = a.ovl_task;
+        march_async<Sys, A, V, DA, FIN, true>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad, &o);
+      } else if (D < 0) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);
       else if (xin) march<Sys, A, V, true, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
       else march<Sys, A, V, false, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
     }
@@ -846,6 +1036,40 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
 
   if (!FIN) return;
   finish_step<NW>(a.ctrl, st, (double)lam_loc, bad != 0u, s_lam, s_bad);
+}
+
+// In-place mode: the overlap strips of one parity from the state itself,
+// after the host loaded or moved the state (layout of OvlLayout; cells past
+// the grid are left alone, nothing reads them as data).
+template <class S>
+__global__ void fill_ovl_kernel(const S *W, int nx, int ny, long long pitch, long long plane, int nv,
+                                int nstrips, int nchunks, int ty, int sw, int ts, S *ovl) {
+  const long long per = (long long)nv * (2 * ty + 2 * sw);
+  const long long total = (long long)nstrips * nchunks * per;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(k / per);
+    const int e = (int)(k - (long long)t * per);
+    const int sx = t % nstrips, cy = t / nstrips;
+    const int X0 = sx * sw, y0 = cy * ty, y1 = min(y0 + ty, ny);
+    const int last = min(X0 + sw, nx) - 1;
+    int j, col, v;
+    if (e < 2 * nv * ty) {
+      const int which = e / (nv * ty), rem = e % (nv * ty);
+      v = rem / ty;
+      j = y0 + rem % ty;
+      col = which == 0 ? X0 : last;
+      if (j >= y1) continue;
+    } else {
+      const int e2 = e - 2 * nv * ty;
+      const int which = e2 / (nv * sw), rem = e2 % (nv * sw);
+      v = rem / sw;
+      col = X0 + rem % sw;
+      j = which == 0 ? y0 : y1 - 1;
+      if (col > last) continue;
+    }
+    ovl[(long long)t * ts + e] = W[(long long)v * plane + (long long)j * pitch + col];
+  }
 }
 
 }  // namespace fv

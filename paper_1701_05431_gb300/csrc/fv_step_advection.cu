@@ -10,7 +10,16 @@ namespace fv {
                         reinterpret_cast<const void *>(&fv_step_kernel<Advection, R, V, TY, NW, true, MB>), \
                         DESC})
 
+#define FV_VARIANT_INPL(R, PREC, V, TY, NW, MB, D, DESC)                                            \
+  out.push_back(Variant{kAdvection, PREC, V, TY, NW, MB, D, async_smem_bytes<R, V, 1, -(D)>(NW),        \
+                        reinterpret_cast<const void *>(&fv_step_kernel<Advection, R, V, TY, NW, true, MB, D, true>), \
+                        DESC, 1})
+
 void register_step_advection(std::vector<Variant> &out) {
+  FV_VARIANT_INPL(double, 0, 2, 32, 4, 2, -4, "advection f64 v2 ty32 w4 b2 async4 inplace");
+  FV_VARIANT_INPL(double, 0, 1, 16, 4, 2, -4, "advection f64 v1 ty16 w4 b2 async4 inplace");
+  FV_VARIANT_INPL(float, 1, 4, 32, 4, 2, -4, "advection f32 v4 ty32 w4 b2 async4 inplace");
+  FV_VARIANT_INPL(float, 1, 2, 16, 4, 2, -4, "advection f32 v2 ty16 w4 b2 async4 inplace");
   FV_VARIANT(double, 0, 2, 32, 4, 1, "advection f64 v2 ty32 w4");
   FV_VARIANT(double, 0, 1, 16, 4, 1, "advection f64 v1 ty16 w4");
   FV_VARIANT(float, 1, 4, 32, 4, 1, "advection f32 v4 ty32 w4");
