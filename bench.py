@@ -320,6 +320,24 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
                 "cell_updates_per_s": 8192 * 8192 * 100 / sec, "ms_per_job": sec * 1e3,
                 "kernel": b.kernel_info()[1], "note": "job = set_state from device + 100 steps, one launch"}
     del pd
+    # f2: the headline job with one state buffer updated in place (halos from
+    # overlap strips) instead of two
+    prim, d = wl.smooth_periodic(8192, dtype=np.float32)
+    pd = torch.from_numpy(prim).to(f"cuda:{local}")
+    for precision in ("f32", "f64"):
+        with fvlib.Solver(d, precision, stream=sptr) as s:
+            s.set_inplace(True)
+
+            def job():
+                s.set_state(pd, primitive=True)
+                s.run(100 if precision == "f32" else 10)
+            sec = timed(job, 1)
+            nsteps = 100 if precision == "f32" else 10
+            out[f"c3_inplace_{precision}"] = {
+                "cell_updates_per_s": 8192 * 8192 * nsteps / sec, "ms_per_job": sec * 1e3,
+                "kernel": s.kernel_info()[1],
+                "note": f"job = set_state from device + {nsteps} steps; one state buffer + overlap strips"}
+    del pd
     # C5: spray moments 2048^2, periodic, 200 steps; FP64 plain and FP32-bulk
     prim, d = wl.spray_field(2048)
     pd = torch.from_numpy(prim).to(f"cuda:{local}")

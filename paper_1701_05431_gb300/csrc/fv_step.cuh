@@ -294,6 +294,12 @@ template <class S> struct Ovl {
   int nstrips, nchunks;
   int X0, y0, y1;  // first column, first and end row of the task
   int ty, ts;      // rows per task, elements per task in one parity
+  // per lane, set once per task by ovl_lane_setup
+  const S *hp;     // halo lanes: source of their used cell in row y0
+  long long hvs;   // its variable stride
+  int hkind, hdir; // 0 state / 2 column strip, Dirichlet side (-1: none)
+  S *wb;           // this task's strips of parity (n + 1) % 2
+  int ecell;       // the lane's cell that is the task's last real column (-1: none)
 };
 
 // Element offsets inside one task's strips (NV variables each).
@@ -375,6 +381,24 @@ static __device__ __forceinline__ const S *inplace_cell(const G &a, const S *W, 
   return W + (long long)j * a.pitch + col;
 }
 
+// Per-lane in-place bookkeeping of one task: where a halo lane's used cell
+// comes from in the task's first row (later rows follow at stride 1 in a
+// column strip or `pitch` in the state), the task's own output strips and
+// the lane's cell holding the task's last real column.
+template <int NV, int N, class G, class S>
+static __device__ __forceinline__ void ovl_lane_setup(const G &a, const S *W, Ovl<S> &o, int X, int lane) {
+  constexpr int SW = 30 * N;
+  o.hp = nullptr;
+  o.hvs = 0;
+  o.hkind = 0;
+  o.hdir = -1;
+  if (lane == 0 || lane == 31)
+    o.hp = inplace_cell<NV, SW>(a, W, o, o.y0, X + (lane == 0 ? N - 1 : 0), o.hvs, o.hdir, o.hkind);
+  o.wb = o.wr + (long long)(o.cy * o.nstrips + o.sx) * o.ts;
+  const int last = min(o.X0 + SW, a.nx) - 1;
+  o.ecell = (last >= X && last < X + N) ? last - X : -1;
+}
+
 // In-place mode: the writer lanes' share of the task's new border strips
 // (row y0 -> south row strip, row y1 - 1 -> north row strip, first and last
 // real column -> west and east column strips), values of W^{n+1} in storage
@@ -383,27 +407,27 @@ template <int NV, int N, class G, class S>
 static __device__ __forceinline__ void write_strips(const G &a, const Ovl<S> &o, int X, int j, const S (&t)[NV][N]) {
   constexpr int SW = 30 * N;
   using L = OvlLayout<NV, SW>;
-  S *base = o.wr + (long long)(o.cy * o.nstrips + o.sx) * o.ts;
-  const int last = min(o.X0 + SW, a.nx) - 1;
   if (j == o.y0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(base + L::rowS(o.ty) + v * SW + (X - o.X0), t[v]);
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + L::rowS(o.ty) + v * SW + (X - o.X0), t[v]);
   }
   if (j == o.y1 - 1) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(base + L::rowN(o.ty) + v * SW + (X - o.X0), t[v]);
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + L::rowN(o.ty) + v * SW + (X - o.X0), t[v]);
   }
   const int jr = j - o.y0;
   if (X == o.X0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) base[L::colW(o.ty) + v * o.ty + jr] = t[v][0];
+    for (int v = 0; v < NV; ++v) o.wb[L::colW(o.ty) + v * o.ty + jr] = t[v][0];
   }
+  if (o.ecell >= 0) {
 #pragma unroll
-  for (int c = 0; c < N; ++c)
-    if (X + c == last) {
+    for (int c = 0; c < N; ++c)
+      if (c == o.ecell) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) base[L::colE(o.ty) + v * o.ty + jr] = t[v][c];
-    }
+        for (int v = 0; v < NV; ++v) o.wb[L::colE(o.ty) + v * o.ty + jr] = t[v][c];
+      }
+  }
 }
 
 // Registers of one row of the march.
@@ -813,10 +837,13 @@ static __device__ __forceinline__ void lring_issue(const G &a,
   cp_async_commit();
 }
 
-// In-place counterpart of lring_issue: own rows of lanes 1..30 (all cells in
-// the grid) are one vector copy per variable from the state, halo rows of
-// those lanes one vector copy per variable from the neighbour's row strip;
-// everything else goes cell by cell through inplace_cell.
+// In-place counterpart of lring_issue.  Lanes 1..30 with all N cells in the
+// grid copy one vector per variable, from the state (own rows, transmissive
+// ghost rows) or from the neighbour's row strip (halo rows); Dirichlet ghost
+// rows are constants.  The halo lanes 0 and 31 fetch only the one cell the
+// task's faces use (lane 0's last, lane 31's first); their other slots keep
+// whatever they held, which only feeds results those lanes never store.
+// Lanes of a ragged last strip that reach past the grid go cell by cell.
 template <class A, int V, int NV, int D, class G>
 static __device__ __forceinline__ void lring_issue_inplace(const G &a, const typename Ops<A>::S *W, int X,
                                                            const Ovl<typename Ops<A>::S> &o,
@@ -826,17 +853,53 @@ static __device__ __forceinline__ void lring_issue_inplace(const G &a, const typ
   constexpr int N = V * Ops<A>::K, SW = 30 * N;
   const int slot = r % D;
   const int lane = threadIdx.x & 31;
-  const bool vec = lane >= 1 && lane <= 30 && X + N <= a.nx;
+  const bool halo_lane = lane == 0 || lane == 31;
+  const int c0 = lane == 0 ? N - 1 : 0;  // the halo lanes' used cell
+  if (j >= o.y0 && j < o.y1) {
+    // an own row (warp-uniform): the state for lanes 1..30, and for the halo
+    // lanes the source found once per task, advanced by the row
+    const int jr = j - o.y0;
+    if (halo_lane) {
+      const S *q = o.hp + (o.hkind == 2 ? (long long)jr : (long long)jr * a.pitch);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        S *d = rg.slot(slot, v) + c0;
+        if (o.hdir >= 0) *d = (S)a.bc_state[o.hdir][v];
+        else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, q + v * o.hvs);
+        else *d = __ldcg(q + v * o.hvs);
+      }
+      cp_async_commit();
+      return;
+    }
+    if (X + N <= a.nx) {
+      const S *q = W + (long long)j * a.pitch + X;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), q + v * a.plane);
+      cp_async_commit();
+      return;
+    }
+  }
   long long vs;
   int dir, kind;
-  // with all N cells in the grid, cell X's source tells where the whole
-  // vector is: a row of the state or of a neighbour's row strip
-  const S *p = inplace_cell<NV, SW>(a, W, o, j, X, vs, dir, kind);
-  if (vec && dir < 0 && kind != 2) {
+  const S *p = inplace_cell<NV, SW>(a, W, o, j, X + c0, vs, dir, kind);
+  if (halo_lane) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      S *d = rg.slot(slot, v) + c0;
+      if (dir >= 0) *d = (S)a.bc_state[dir][v];
+      else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, p + v * vs);
+      else *d = __ldcg(p + v * vs);
+    }
+  } else if (dir >= 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = (S)a.bc_state[dir][v];
+  } else if (X + N <= a.nx && kind != 2) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * vs);
   } else {
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < N; ++c) {
       const S *q = inplace_cell<NV, SW>(a, W, o, j, X + c, vs, dir, kind);
 #pragma unroll
@@ -1027,6 +1090,7 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
         o.y1 = y1;
         o.ty = TY;
         o.ts = a.ovl_task;
+        ovl_lane_setup<NV, N>(a, src, o, X, lane);
         march_async<Sys, A, V, DA, FIN, true>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad, &o);
       } else if (D < 0) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);
       else if (xin) march<Sys, A, V, true, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);

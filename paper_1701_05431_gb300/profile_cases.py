@@ -1,6 +1,6 @@
 """Small, self-contained invocations of each kernel, for profiling with ncu.
 
-  python -m paper_1701_05431_gb300.profile_cases step --system euler --precision f32 --n 4096 --steps 3
+  python -m paper_1701_05431_gb300.profile_cases step --system euler --precision f32 --n 4096 --steps 3 [--inplace]
   python -m paper_1701_05431_gb300.profile_cases batch --instances 96 --steps 4 --tune 2
   python -m paper_1701_05431_gb300.profile_cases spray --precision f64 --n 1024 --steps 3
   python -m paper_1701_05431_gb300.profile_cases sweep --workload c3 --precision f32
@@ -30,7 +30,7 @@ def _device(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def step_case(system: str, precision: str, n: int, steps: int, tune: int) -> str:
+def step_case(system: str, precision: str, n: int, steps: int, tune: int, inplace: bool = False) -> str:
     import torch
     import workloads as wl
     from paper_1701_05431_gb300 import fvlib
@@ -42,6 +42,8 @@ def step_case(system: str, precision: str, n: int, steps: int, tune: int) -> str
         prim, d = wl.spray_field(n)
     stream = torch.cuda.current_stream().cuda_stream
     with fvlib.Solver(d, precision, stream=stream, tune=tune) as s:
+        if inplace:
+            s.set_inplace(True)
         s.set_state(_device(prim), primitive=True)
         s.run(steps)
         torch.cuda.synchronize()
@@ -127,12 +129,13 @@ def main(argv=None):
     ap.add_argument("--instances", type=int, default=96)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--tune", type=int, default=0)
+    ap.add_argument("--inplace", action="store_true", help="step case: one state buffer (fv_set_inplace)")
     a = ap.parse_args(argv)
     if a.case == "sweep":
         sweep(a.workload, a.precision, a.steps)
         return
     if a.case == "step":
-        k = step_case(a.system, a.precision, a.n, a.steps, a.tune)
+        k = step_case(a.system, a.precision, a.n, a.steps, a.tune, a.inplace)
     elif a.case == "spray":
         k = step_case("spray", a.precision, a.n, a.steps, a.tune)
     else:
