@@ -308,6 +308,19 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
         out["c3_fixed_dt_per_step_launches_f32"] = {"cell_updates_per_s": 8192 * 8192 * 100 / sec,
                                                     "ms_per_job": sec * 1e3, "kernel": s.kernel_info()[1],
                                                     "note": "job = set_state from device + 100 steps"}
+    for precision in ("f32", "bf16"):
+        with fvlib.Solver(dfix, precision, stream=sptr) as s:
+            s.set_time_blocking(2)
+
+            def job():
+                s.set_state(pd, primitive=True)
+                s.run(100)
+            sec = timed(job, 1)
+            out[f"c3_fixed_dt_two_steps_per_launch_{precision}"] = {
+                "cell_updates_per_s": 8192 * 8192 * 100 / sec, "ms_per_job": sec * 1e3,
+                "algorithmic_bytes_per_cell_update": (16 if precision == "f32" else 8),
+                "kernel": "two-step passes (fv_set_time_blocking)",
+                "note": "job = set_state from device + 100 steps = 50 launches"}
     for mode in ("gated", "dataflow"):
         with fvlib.Batch([dfix], "f32", stream=sptr, tune=1) as b:
             b.set_dataflow(mode == "dataflow")

@@ -146,6 +146,20 @@ fv_status fv_run(fv_ctx *ctx, int nsteps, double t_end, double *t_out);
  * memory owned by the caller.  Synchronises the stream. */
 fv_status fv_get_state(fv_ctx *ctx, void *dst, int dst_is_device, int dst_dtype);
 
+/* Time blocking: steps_per_pass = 2 advances two time steps per kernel
+ * launch, reading and writing the state once per two steps (half the bytes
+ * per cell-update).  Needs the paper's fixed dt (fixed_dt > 0, Sec. 2.2.1)
+ * and periodic boundaries on all four sides, advection or Euler, not in
+ * place.  Results, times, step counts and errors are bit for bit those of
+ * one step per launch: a pass that finds the intermediate state failing the
+ * paper's check dt lmax <= min(dx, dy) (or inadmissible) leaves everything
+ * as it was and the steps from there run one at a time.  fv_run uses passes
+ * when t_end <= 0 and at least two steps remain.  steps_per_pass = 1 turns
+ * it off.  With tune >= 2 the (tune - 2)-th two-step kernel candidate is
+ * used (FV_ERR_INVALID_ARG past the last one), else the first that fills
+ * the GPU.  Errors: FV_ERR_INVALID_ARG when a condition above fails. */
+fv_status fv_set_time_blocking(fv_ctx *ctx, int steps_per_pass);
+
 /* In-place mode (on != 0; advection and Euler, every precision): the
  * context keeps ONE state buffer instead of two and updates it in place.
  * Each warp task writes, besides its cells, its border rows and columns of

@@ -35,7 +35,7 @@ struct Ctrl {
   unsigned int blocks_done;
   unsigned int err_pending;   // raised by any block during a step
   unsigned int err_committed; // folded in by the step's last block
-  unsigned int pad_;
+  unsigned int cur;           // buffer (0/1) that holds W^step (single-instance contexts)
 };
 
 template <class R> struct Ops;
@@ -420,6 +420,7 @@ struct StepStart {
   long long step;
   unsigned err;
   int run;
+  unsigned cur;  // buffer holding W^step
 };
 
 static __device__ __forceinline__ StepStart read_step_start(const DtPolicy &pol, Ctrl *ctrl) {
@@ -432,6 +433,7 @@ static __device__ __forceinline__ StepStart read_step_start(const DtPolicy &pol,
   StepStart s;
   s.dt = 0.0;
   s.step = c.step;
+  s.cur = __ldcg(&ctrl->cur);
   s.run = choose_dt(pol, c, lam, &s.dt, &s.err) ? 1 : 0;
   return s;
 }
@@ -478,6 +480,7 @@ static __device__ __forceinline__ void finish_step(Ctrl *ctrl, const StepStart &
       ctrl->t = __ldcg(&ctrl->t) + st.dt;
       ctrl->dt_last = st.dt;
       ctrl->step = n + 1;
+      ctrl->cur = st.cur ^ 1u;
       ctrl->lam[(n + 2) % 3] = 0ull;
     }
     if (e) ctrl->err_committed |= e;

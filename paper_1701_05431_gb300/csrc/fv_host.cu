@@ -16,6 +16,7 @@
 #include "../../include/fv.h"
 #include "fv_internal.h"
 #include "fv_step.cuh"
+#include "fv_tb.cuh"
 
 namespace fv {
 
@@ -49,6 +50,9 @@ struct fv_ctx {
   size_t esize = 0;
   long long pitch = 0, plane = 0;
   size_t buf_bytes = 0;
+  // two time steps per launch (fixed dt, periodic): its kernel and grid
+  int tb_variant = -1;
+  int tb_grid = 0;
   // in-place mode: buf[1] == buf[0], overlap strips of the two parities
   bool inplace = false;
   void *ovl = nullptr;
@@ -164,7 +168,7 @@ static fv_status validate(const fv_config *c) {
 static int default_variant(int system, int prec) {
   const auto &vs = all_variants();
   for (size_t k = 0; k < vs.size(); ++k)
-    if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace) return (int)k;
+    if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace && !vs[k].tb) return (int)k;
   return -1;
 }
 
@@ -184,13 +188,13 @@ static int resident_blocks(const Variant &V) {
 // precision), in the table's order of preference, whose warp tasks fill the
 // GPU (at least two per resident warp); if none does, the one with the most
 // tasks per resident warp.
-static int default_variant_for(int system, int prec, int nx, int ny, int sms, int inplace = 0) {
+static int default_variant_for(int system, int prec, int nx, int ny, int sms, int inplace = 0, int tb = 0) {
   const auto &vs = all_variants();
   int best = -1;
   double best_ratio = -1.0;
   for (size_t k = 0; k < vs.size(); ++k) {
     const Variant &V = vs[k];
-    if (V.system != system || V.precision != prec || V.inplace != inplace) continue;
+    if (V.system != system || V.precision != prec || V.inplace != inplace || V.tb != tb) continue;
     const double tasks = (double)((nx + 30 * V.V - 1) / (30 * V.V)) * (double)((ny + V.TY - 1) / V.TY);
     const double ratio = tasks / ((double)resident_blocks(V) * V.NW * sms);
     if (ratio >= 2.0) return (int)k;
@@ -206,7 +210,7 @@ static std::vector<int> candidates(int system, int prec) {
   std::vector<int> out;
   const auto &vs = all_variants();
   for (size_t k = 0; k < vs.size(); ++k)
-    if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace) out.push_back((int)k);
+    if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace && !vs[k].tb) out.push_back((int)k);
   return out;
 }
 
@@ -327,8 +331,32 @@ static fv_status launch_step(fv_ctx *c, cudaStream_t s) {
   return FV_OK;
 }
 
-static fv_status get_graph(fv_ctx *c, int nsteps, cudaGraphExec_t *out) {
-  auto it = c->graphs.find(nsteps);
+// One two-step pass (fv_tb.cuh) on stream s.
+static fv_status launch_tb(fv_ctx *c, cudaStream_t s) {
+  const Variant &V = all_variants()[c->tb_variant];
+  dim3 grid(c->tb_grid), block(V.NW * 32);
+  cudaError_t e;
+  if (V.precision == 0) {
+    StepArgs<double> a = make_args<double>(c, V);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
+  } else if (V.precision == 1) {
+    StepArgs<float> a = make_args<float>(c, V);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
+  } else {
+    StepArgs<__nv_bfloat16> a = make_args<__nv_bfloat16>(c, V);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "two-step kernel launch");
+  return FV_OK;
+}
+
+// Graphs of n single steps (key n) or of n two-step passes (key -n).
+static fv_status get_graph(fv_ctx *c, int nsteps, cudaGraphExec_t *out, bool passes = false) {
+  const int key = passes ? -nsteps : nsteps;
+  auto it = c->graphs.find(key);
   if (it != c->graphs.end()) {
     *out = it->second;
     return FV_OK;
@@ -336,7 +364,7 @@ static fv_status get_graph(fv_ctx *c, int nsteps, cudaGraphExec_t *out) {
   if (c->graphs.size() > 16) free_graphs(c);
   FV_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   fv_status st = FV_OK;
-  for (int k = 0; k < nsteps && st == FV_OK; ++k) st = launch_step(c, c->cap_stream);
+  for (int k = 0; k < nsteps && st == FV_OK; ++k) st = passes ? launch_tb(c, c->cap_stream) : launch_step(c, c->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (st != FV_OK) {
@@ -348,7 +376,7 @@ static fv_status get_graph(fv_ctx *c, int nsteps, cudaGraphExec_t *out) {
   e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-  c->graphs[nsteps] = ge;
+  c->graphs[key] = ge;
   *out = ge;
   return FV_OK;
 }
@@ -522,18 +550,19 @@ static fv_status fill_ovl(fv_ctx *c, long long step) {
   return FV_OK;
 }
 
-static fv_status seed(fv_ctx *c, long long step, double t) {
+static fv_status seed(fv_ctx *c, long long step, double t, unsigned cur) {
   Ctrl h;
   std::memset(&h, 0, sizeof(h));
   h.step = step;
   h.t = t;
+  h.cur = cur;
   *c->h_ctrl = h;
   FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
   if (c->lamw)  // all-ones bytes are NaNs: every cell starts its Newton solve cold
     FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 4 * c->plane, c->stream));
   double p0 = c->cfg.params[0], p1 = c->cfg.params[1];
   if (c->cfg.system == FV_EULER) p1 = c->cfg.params[0] - 1.0;
-  FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision, c->buf[step & 1],
+  FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision, c->buf[cur],
                                 c->cfg.nx, c->cfg.ny, c->pitch, c->plane, p0, p1, c->ctrl,
                                 (int)(step % 3), c->stream));
   fv_status st = read_ctrl(c);
@@ -571,7 +600,7 @@ extern "C" fv_status fv_set_state(fv_ctx *c, const void *src, int src_is_device,
   FV_CUDA(c, launch_load_state(c->cfg.system, prec, dsrc, src_dtype == FV_F32, layout == FV_PRIMITIVE,
                                c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->cfg.params[0],
                                c->stream));
-  return seed(c, 0, 0.0);
+  return seed(c, 0, 0.0, 0u);
 }
 
 extern "C" fv_status fv_get_state(fv_ctx *c, void *dst, int dst_is_device, int dst_dtype) {
@@ -581,7 +610,7 @@ extern "C" fv_status fv_get_state(fv_ctx *c, void *dst, int dst_is_device, int d
   if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
   fv_status st = read_ctrl(c);
   if (st != FV_OK) return st;
-  const void *cur = c->buf[c->h_ctrl->step & 1];
+  const void *cur = c->buf[c->h_ctrl->cur];
   const int prec = c->cfg.precision;
   const size_t dsz = dst_dtype == FV_F64 ? 8 : 4;
   const bool same = (dst_dtype == FV_F64 && prec == 0) || (dst_dtype == FV_F32 && prec == 1);
@@ -633,7 +662,7 @@ extern "C" fv_status fv_snapshot(fv_ctx *c, void *dst, int dst_dtype) {
   }
   // the previous host copy must be done before the staging buffer is refilled
   if (c->snap_pending) FV_CUDA(c, cudaStreamWaitEvent(c->stream, c->snap_done, 0));
-  const void *cur = c->buf[c->h_ctrl->step & 1];
+  const void *cur = c->buf[c->h_ctrl->cur];
   FV_CUDA(c, launch_store_state(c->cfg.precision, c->nvar, cur, c->snap_buf, dst_dtype == FV_F32, c->cfg.nx,
                                 c->cfg.ny, c->pitch, c->plane, c->stream));
   FV_CUDA(c, cudaEventRecord(c->snap_ready, c->stream));
@@ -715,6 +744,31 @@ extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) 
                              c->stream));
   const int chunk = 64;
   int left = nsteps;
+  if (c->tb_variant >= 0 && t_end <= 0.0 && nsteps >= 2) {
+    // two steps per launch; a pass that finds W^{n+1} failing the paper's
+    // check leaves everything as it was and flags kErrReplay, and the steps
+    // from there are run one at a time (stopping where they would have)
+    fv_status st = read_ctrl(c);
+    if (st != FV_OK) return st;
+    const long long start = c->h_ctrl->step;
+    int passes = nsteps / 2;
+    while (passes > 0) {
+      const int n = passes >= chunk / 2 ? chunk / 2 : passes;
+      cudaGraphExec_t g;
+      st = get_graph(c, n, &g, true);
+      if (st != FV_OK) return st;
+      FV_CUDA(c, cudaGraphLaunch(g, c->stream));
+      passes -= n;
+    }
+    st = read_ctrl(c);
+    if (st != FV_OK) return st;
+    if (c->h_ctrl->err_committed & kErrReplay) {
+      c->h_ctrl->err_committed &= ~kErrReplay;
+      FV_CUDA(c, cudaMemcpyAsync(&c->ctrl->err_committed, &c->h_ctrl->err_committed, sizeof(unsigned),
+                                 cudaMemcpyHostToDevice, c->stream));
+    }
+    left = nsteps - (int)(c->h_ctrl->step - start);
+  }
   while (left > 0) {
     const int n = left >= chunk ? chunk : left;
     cudaGraphExec_t g;
@@ -727,6 +781,48 @@ extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) 
   if (st != FV_OK) return st;
   if (t_out) *t_out = c->h_ctrl->t;
   return status_of_flags(c, c->h_ctrl->err_committed);
+}
+
+extern "C" fv_status fv_set_time_blocking(fv_ctx *c, int steps_per_pass) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (steps_per_pass == 1) {
+    c->tb_variant = -1;
+    free_graphs(c);
+    return FV_OK;
+  }
+  if (steps_per_pass != 2) return fail(c, FV_ERR_INVALID_ARG, "steps per pass must be 1 or 2");
+  if (!(c->cfg.fixed_dt > 0.0)) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass need the fixed-dt mode");
+  for (int s = 0; s < 4; ++s)
+    if (c->cfg.bc[s] != FV_BC_PERIODIC) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass need a periodic grid");
+  if (c->inplace) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass do not run in place");
+  int vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 0, 2);
+  if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "no two-step kernel for this system and precision");
+  if (c->cfg.tune >= 2) {
+    // a forced candidate: the (tune - 2)-th two-step kernel of (system, precision)
+    const auto &vs = all_variants();
+    int k = 0;
+    vi = -1;
+    for (size_t q = 0; q < vs.size(); ++q)
+      if (vs[q].system == c->cfg.system && vs[q].precision == c->cfg.precision && vs[q].tb == 2 &&
+          k++ == c->cfg.tune - 2) {
+        vi = (int)q;
+        break;
+      }
+    if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "tune index out of range for two-step kernels");
+  }
+  const Variant &V = all_variants()[vi];
+  if (V.smem > 0)
+    FV_CUDA(c, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
+  int nb = 0;
+  FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));
+  if (nb < 1) return fail(c, FV_ERR_CUDA, std::string("kernel cannot launch: ") + V.desc);
+  const long long ntasks = (long long)((c->cfg.nx + 30 * V.V - 1) / (30 * V.V)) * ((c->cfg.ny + V.TY - 1) / V.TY);
+  long long grid = (long long)nb * c->sms, need = (ntasks + V.NW - 1) / V.NW;
+  if (need < grid) grid = need;
+  c->tb_variant = vi;
+  c->tb_grid = (int)(grid < 1 ? 1 : grid);
+  free_graphs(c);
+  return FV_OK;
 }
 
 extern "C" fv_status fv_step(fv_ctx *c, double *dt_used) {
@@ -747,7 +843,7 @@ extern "C" fv_status fv_totals(fv_ctx *c, double *totals) {
   fv_status st = read_ctrl(c);
   if (st != FV_OK) return st;
   const int nb = totals_blocks(c->cfg.ny);
-  FV_CUDA(c, launch_totals(c->cfg.precision, c->nvar, c->buf[c->h_ctrl->step & 1],
+  FV_CUDA(c, launch_totals(c->cfg.precision, c->nvar, c->buf[c->h_ctrl->cur],
                            c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->partials, nb, c->d_totals,
                            c->dx * c->dy, c->stream));
   FV_CUDA(c, cudaMemcpyAsync(c->h_scalar, c->d_totals, sizeof(double) * c->nvar, cudaMemcpyDeviceToHost,
@@ -772,13 +868,8 @@ extern "C" fv_status fv_set_time(fv_ctx *c, double t, long long step) {
   if (step < 0 || !std::isfinite(t)) return fail(c, FV_ERR_INVALID_ARG, "bad time or step");
   fv_status st = read_ctrl(c);
   if (st != FV_OK) return st;
-  const long long cur = c->h_ctrl->step;
-  if ((cur & 1) != (step & 1) && c->buf[0] != c->buf[1]) {
-    // the state lives in buffer step % 2: move it to the new parity
-    FV_CUDA(c, cudaMemcpyAsync(c->buf[step & 1], c->buf[cur & 1], c->buf_bytes, cudaMemcpyDeviceToDevice,
-                               c->stream));
-  }
-  return seed(c, step, t);
+  // the state stays in its buffer
+  return seed(c, step, t, c->h_ctrl->cur);
 }
 
 extern "C" fv_status fv_lambda_max(fv_ctx *c, double *lmax) {
@@ -846,6 +937,7 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
   on = on ? 1 : 0;
   if (on == (int)c->inplace) return FV_OK;
   if (c->cfg.system == FV_SPRAY) return fail(c, FV_ERR_INVALID_ARG, "in-place mode: advection and Euler only");
+  if (on && c->tb_variant >= 0) return fail(c, FV_ERR_INVALID_ARG, "in-place mode does not run two steps per pass");
   long long step = 0;
   if (c->has_state) {
     fv_status st = read_ctrl(c);
@@ -865,8 +957,12 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
     void *ovl = nullptr;
     cudaError_t e = cudaMalloc(&ovl, 2 * pb);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(overlap strips)");
-    if (c->has_state && (step & 1))
+    if (c->has_state && c->h_ctrl->cur == 1u) {
+      // the state goes to buffer 0, which becomes the only one
       FV_CUDA(c, cudaMemcpyAsync(c->buf[0], c->buf[1], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+      c->h_ctrl->cur = 0u;
+      FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+    }
     FV_CUDA(c, cudaStreamSynchronize(c->stream));
     cudaFree(c->buf[1]);
     c->buf[1] = c->buf[0];
@@ -882,8 +978,11 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
   void *b1 = nullptr;
   cudaError_t e = cudaMalloc(&b1, c->buf_bytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(state)");
-  if (c->has_state && (step & 1))
-    FV_CUDA(c, cudaMemcpyAsync(b1, c->buf[0], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->has_state && c->h_ctrl->cur != 0u) {
+    // in place both indices name buffer 0, where the state is
+    c->h_ctrl->cur = 0u;
+    FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+  }
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->buf[1] = b1;
   cudaFree(c->ovl);

@@ -24,6 +24,7 @@ struct Variant {
   const void *kernel;
   const char *desc;
   int inplace;     // 1: in-place kernel (one state buffer plus overlap strips)
+  int tb;          // 2: two time steps per launch (fixed dt, periodic); 0: one
 };
 
 // Registration hooks, one per translation unit of step kernels.

@@ -220,7 +220,7 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
   double lmax = 0.0;
   bool bad = false;
   if (st.run) {
-    R *__restrict__ W = ((st.step + 1) & 1) ? a.buf1 : a.buf0;  // the transport output
+    R *__restrict__ W = st.cur ? a.buf0 : a.buf1;  // the transport output
     const double dt = st.dt;
     const long long ncell = (long long)a.nx * a.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;

@@ -1059,8 +1059,8 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
   if (st.run) {
     const long long n = st.step;
     // in place: buf0 == buf1, so src == dst
-    const S *src = (n & 1) ? a.buf1 : a.buf0;
-    S *dst = (n & 1) ? a.buf0 : a.buf1;
+    const S *src = st.cur ? a.buf1 : a.buf0;
+    S *dst = st.cur ? a.buf0 : a.buf1;
     const SysParams<A> P = splat_params<A>(a.sp);
     // half steps: the face fluxes are carried doubled (see lf_face2)
     const A lx = Ops<A>::splat((typename Ops<A>::P)(0.5 * (st.dt / a.dx)));

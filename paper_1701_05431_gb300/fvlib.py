@@ -59,7 +59,7 @@ _lib = None
 EXPORTS = ("fv_status_string", "fv_last_error", "fv_init", "fv_destroy", "fv_set_state", "fv_step",
            "fv_run", "fv_get_state", "fv_totals", "fv_time", "fv_set_time", "fv_lambda_max",
            "fv_kernel_info", "fv_kernel_candidate", "fv_gauss_legendre", "fv_snapshot",
-           "fv_snapshot_wait", "fv_set_inplace")
+           "fv_snapshot_wait", "fv_set_inplace", "fv_set_time_blocking")
 
 
 def library_path() -> str:
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.fv_snapshot.argtypes = [vp, vp, ctypes.c_int]
     L.fv_snapshot_wait.argtypes = [vp]
     L.fv_set_inplace.argtypes = [vp, ctypes.c_int]
+    L.fv_set_time_blocking.argtypes = [vp, ctypes.c_int]
     L.fv_time.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.fv_set_time.argtypes = [vp, ctypes.c_double, ctypes.c_longlong]
     L.fv_lambda_max.argtypes = [vp, dp]
@@ -261,6 +262,11 @@ class Solver:
             raise ValueError("snapshot target must be host memory")
         _check(self.lib.fv_snapshot(self.ctx, p, _dtype_code(dst)), self.ctx, self.lib)
         return dst
+
+    def set_time_blocking(self, steps_per_pass: int = 2):
+        """Two time steps per kernel launch (fixed dt, periodic grids; same
+        results as one step per launch)."""
+        _check(self.lib.fv_set_time_blocking(self.ctx, int(steps_per_pass)), self.ctx, self.lib)
 
     def set_inplace(self, on: bool = True):
         """One state buffer updated in place, halos from overlap strips
