@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -69,7 +70,9 @@ class Clocks:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to FV_CLOCKS_DIR (default: the system's temporary directory)
+        d = os.environ.get("FV_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"fv_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -319,7 +322,7 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
             out[f"c3_fixed_dt_two_steps_per_launch_{precision}"] = {
                 "cell_updates_per_s": 8192 * 8192 * 100 / sec, "ms_per_job": sec * 1e3,
                 "algorithmic_bytes_per_cell_update": (16 if precision == "f32" else 8),
-                "kernel": "two-step passes (fv_set_time_blocking)",
+                "kernel": s.two_step_kernel(),
                 "note": "job = set_state from device + 100 steps = 50 launches"}
     for mode in ("gated", "dataflow"):
         with fvlib.Batch([dfix], "f32", stream=sptr, tune=1) as b:

@@ -213,6 +213,10 @@ fv_status fv_lambda_max(fv_ctx *ctx, double *lmax);
  * static description such as "f32 v2 ty32 w4". */
 fv_status fv_kernel_info(fv_ctx *ctx, int *variant, const char **desc);
 
+/* Description of the two-step kernel fv_run uses (fv_set_time_blocking),
+ * NULL when one step per launch is in force or ctx is NULL. */
+const char *fv_kernel_info_two_step(const fv_ctx *ctx);
+
 /* Description of compiled kernel candidate `index` (0-based) for a system
  * and precision, e.g. "euler f32 v1 ty64 w4 b6": V cells per lane, TY rows
  * per warp task, NW warps per block, register budget for b blocks per SM.

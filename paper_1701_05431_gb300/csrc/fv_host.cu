@@ -895,6 +895,11 @@ extern "C" fv_status fv_kernel_info(fv_ctx *c, int *variant, const char **desc) 
   return FV_OK;
 }
 
+extern "C" const char *fv_kernel_info_two_step(const fv_ctx *c) {
+  if (!c || c->tb_variant < 0) return nullptr;
+  return all_variants()[c->tb_variant].desc;
+}
+
 // Gauss-Legendre rule on [0,1]: roots of P_Q by Newton's method on the
 // three-term recurrence, weights 2/((1 - t^2) P_Q'(t)^2) halved for [0,1].
 extern "C" fv_status fv_gauss_legendre(int Q, double *x, double *w) {

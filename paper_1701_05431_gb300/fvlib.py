@@ -59,7 +59,7 @@ _lib = None
 EXPORTS = ("fv_status_string", "fv_last_error", "fv_init", "fv_destroy", "fv_set_state", "fv_step",
            "fv_run", "fv_get_state", "fv_totals", "fv_time", "fv_set_time", "fv_lambda_max",
            "fv_kernel_info", "fv_kernel_candidate", "fv_gauss_legendre", "fv_snapshot",
-           "fv_snapshot_wait", "fv_set_inplace", "fv_set_time_blocking")
+           "fv_snapshot_wait", "fv_set_inplace", "fv_set_time_blocking", "fv_kernel_info_two_step")
 
 
 def library_path() -> str:
@@ -93,6 +93,8 @@ def load(build_if_missing: bool = True):
     L.fv_snapshot_wait.argtypes = [vp]
     L.fv_set_inplace.argtypes = [vp, ctypes.c_int]
     L.fv_set_time_blocking.argtypes = [vp, ctypes.c_int]
+    L.fv_kernel_info_two_step.argtypes = [vp]
+    L.fv_kernel_info_two_step.restype = ctypes.c_char_p
     L.fv_time.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.fv_set_time.argtypes = [vp, ctypes.c_double, ctypes.c_longlong]
     L.fv_lambda_max.argtypes = [vp, dp]
@@ -100,7 +102,7 @@ def load(build_if_missing: bool = True):
     L.fv_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
     L.fv_kernel_candidate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p)]
     for name in EXPORTS:
-        if name not in ("fv_status_string", "fv_last_error", "fv_destroy"):
+        if name not in ("fv_status_string", "fv_last_error", "fv_destroy", "fv_kernel_info_two_step"):
             getattr(L, name).restype = ctypes.c_int
     L.fv_totals_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, vp, vp]
@@ -267,6 +269,11 @@ class Solver:
         """Two time steps per kernel launch (fixed dt, periodic grids; same
         results as one step per launch)."""
         _check(self.lib.fv_set_time_blocking(self.ctx, int(steps_per_pass)), self.ctx, self.lib)
+
+    def two_step_kernel(self):
+        """Description of the two-step kernel in use, or None."""
+        d = self.lib.fv_kernel_info_two_step(self.ctx)
+        return d.decode() if d else None
 
     def set_inplace(self, on: bool = True):
         """One state buffer updated in place, halos from overlap strips
