@@ -514,25 +514,29 @@ def main():
         s.run(nsteps_job)
         s.get_state(h_out)
         k = max(1, min(args.steps, 3))
+        # each job: inputs copied in from pinned host memory, 100 steps, the
+        # result copied out; the copy out is an asynchronous snapshot, so it
+        # overlaps the next job (the last one is waited for inside the region)
+        s.snapshot(h_out)
+        s.snapshot_wait()
         barrier()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
         for _ in range(k):
             s.set_state(h_in, primitive=True)
             s.run(nsteps_job)
-            s.get_state(h_out)
-        ev1.record(stream)
-        barrier()
+            s.snapshot(h_out)
+        s.snapshot_wait()
+        torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        ms = ev0.elapsed_time(ev1)
+        wall = max_over_ranks(wall, f"cuda:{local}")
         s.close()
-        out["e2e"] = {"value": ncell * nsteps_job * k * ws / (ms / 1e3), "unit": "cell-updates/s",
+        out["e2e"] = {"value": ncell * nsteps_job * k * ws / wall, "unit": "cell-updates/s",
                       "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4),
                       "wall_s": wall, "steps": k,
-                      "path": "fv_set_state(pinned host f32 primitive) + fv_run + fv_get_state(pinned host f32)"}
-        out["e2e"]["gpu_launches"] = k * (nsteps_job + 2)
+                      "path": "fv_set_state(pinned host f32 primitive) + fv_run + fv_snapshot(pinned host f32, "
+                              "asynchronous, overlapping the next job) + fv_snapshot_wait; host wall clock"}
+        out["e2e"]["gpu_launches"] = k * (nsteps_job + 3)
 
     # ---- accuracy of the timed configuration against stored oracle samples
     golden = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle_samples.npz")
