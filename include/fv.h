@@ -169,7 +169,9 @@ fv_status fv_set_time_blocking(fv_ctx *ctx, int steps_per_pass);
  * by step parity, so no task reads a value another is overwriting.  Results
  * are bit for bit those of the default mode.  Switching frees (on) or
  * allocates again (off) the second state buffer and keeps the current state,
- * time and step.  Autotuning (tune = 1) is not done in place.
+ * time and step.  Autotuning (tune = 1) is not done in place; with
+ * tune >= 2 the (tune - 2)-th in-place kernel candidate is used
+ * (FV_ERR_INVALID_ARG past the last one), else the first that fills the GPU.
  * Errors: FV_ERR_INVALID_ARG (spray system), FV_ERR_OOM, FV_ERR_CUDA. */
 fv_status fv_set_inplace(fv_ctx *ctx, int on);
 

@@ -66,7 +66,7 @@ struct fv_ctx {
   size_t staging_bytes = 0;
   double *partials = nullptr;
   double *d_totals = nullptr;
-  double *lamw = nullptr;        // spray: warm-start multipliers (4 planes)
+  double *lamw = nullptr;        // spray: multipliers of the last two solves (8 planes)
   double *nodes = nullptr;       // spray: quadrature table
   int spray_Q = 0;
   int src_grid = 0;
@@ -455,7 +455,7 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     if ((e = cudaMalloc(&c->nodes, sizeof(double) * tab.size())) != cudaSuccess) return bail(e, "cudaMalloc(nodes)");
     if ((e = cudaMemcpy(c->nodes, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(e, "cudaMemcpy(nodes)");
-    if ((e = cudaMalloc(&c->lamw, sizeof(double) * 4 * c->plane)) != cudaSuccess) return bail(e, "cudaMalloc(lamw)");
+    if ((e = cudaMalloc(&c->lamw, sizeof(double) * 8 * c->plane)) != cudaSuccess) return bail(e, "cudaMalloc(lamw)");
     c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, Q, c->sms);
   }
   int prec = cfg->precision;  // 0 f64, 1 f32, 2 bf16 storage
@@ -559,7 +559,7 @@ static fv_status seed(fv_ctx *c, long long step, double t, unsigned cur) {
   *c->h_ctrl = h;
   FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
   if (c->lamw)  // all-ones bytes are NaNs: every cell starts its Newton solve cold
-    FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 4 * c->plane, c->stream));
+    FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 8 * c->plane, c->stream));
   double p0 = c->cfg.params[0], p1 = c->cfg.params[1];
   if (c->cfg.system == FV_EULER) p1 = c->cfg.params[0] - 1.0;
   FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision, c->buf[cur],
@@ -951,8 +951,21 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
   }
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
   if (on) {
-    const int vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 1);
+    int vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 1);
     if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "no in-place kernel for this system and precision");
+    if (c->cfg.tune >= 2) {
+      // a forced candidate: the (tune - 2)-th in-place kernel of (system, precision)
+      const auto &vs = all_variants();
+      int k = 0;
+      vi = -1;
+      for (size_t q = 0; q < vs.size(); ++q)
+        if (vs[q].system == c->cfg.system && vs[q].precision == c->cfg.precision && vs[q].inplace &&
+            k++ == c->cfg.tune - 2) {
+          vi = (int)q;
+          break;
+        }
+      if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "tune index out of range for in-place kernels");
+    }
     const Variant &V = all_variants()[vi];
     const int sw = 30 * V.V;
     const long long ntasks = (long long)((c->cfg.nx + sw - 1) / sw) * ((c->cfg.ny + V.TY - 1) / V.TY);

@@ -10,8 +10,10 @@
 // Hankel-type moment matrices loses too many digits); the moments of a trial
 // density are Gauss-Legendre sums in x = sqrt(S) whose nodes and
 // pre-multiplied weights sit in shared memory.  The multipliers of each cell
-// are kept between steps (warm start): the moments move by O(dt) per step, so
-// Newton usually needs three or four moment evaluations instead of eight.
+// are kept between steps (warm start), those of the two last steps, and the
+// solve starts from their linear extrapolation: the moments move smoothly,
+// by O(dt) per step, so Newton usually needs two or three moment evaluations
+// instead of eight.
 // Only the first evaluation of a solve computes the Q exponentials
 // e_q = exp(-p(x_q)) (p the multipliers' polynomial); they stay in shared
 // memory, and after a Newton step d with sum |d_k| <= 2^-10 the next
@@ -36,7 +38,7 @@ template <class R> struct SourceArgs {
   R *buf0;
   R *buf1;
   Ctrl *ctrl;
-  double *lamw;          // 4 planes of ny x pitch warm-start multipliers
+  double *lamw;          // 8 planes of ny x pitch: multipliers of the last two solves
   const double *nodes;   // Q x kNodeStride
   int nx, ny;
   long long pitch, plane;
@@ -232,14 +234,26 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
       for (int v = 0; v < 6; ++v) w[v] = (double)W[v * a.plane + o];
       const double m[4] = {w[0], w[1], w[2], w[3]};
       bool cell_bad = !realizable(m);
-      double lam[4];
-      const double warm0 = a.lamw[o];
+      // start from the multipliers of the last solve, extrapolated linearly
+      // in time from the two last solves when both exist (the moments move
+      // smoothly from step to step, so the start is closer by an order of dt)
+      double lam[4], lam_prev[4];
+      const double warm0 = a.lamw[o], prev0 = a.lamw[4 * a.plane + o];
       if (warm0 == warm0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) lam[q] = a.lamw[q * a.plane + o];
+        for (int q = 0; q < 4; ++q) {
+          lam_prev[q] = a.lamw[q * a.plane + o];
+          lam[q] = lam_prev[q];
+        }
+        if (prev0 == prev0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) lam[q] = 2.0 * lam_prev[q] - a.lamw[(4 + q) * a.plane + o];
+        }
       } else {
         lam[0] = -log(m[0]);
         lam[1] = lam[2] = lam[3] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lam_prev[q] = __longlong_as_double(0x7ff8000000000000LL);
       }
       double n0 = 0.0, mmh = 0.0;
       if (!cell_bad) cell_bad = !maxent(s_nodes, a.Q, a.tol, m, lam, n0, mmh, s_exp + threadIdx.x, kSrcThreads);
@@ -276,9 +290,13 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
         cell_bad |= b != 0u;
         lmax = fmax(lmax, (double)l);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) a.lamw[q * a.plane + o] = lam[q];
+        for (int q = 0; q < 4; ++q) {
+          a.lamw[(4 + q) * a.plane + o] = lam_prev[q];
+          a.lamw[q * a.plane + o] = lam[q];
+        }
       } else {
         a.lamw[o] = __longlong_as_double(0x7ff8000000000000LL);
+        a.lamw[4 * a.plane + o] = __longlong_as_double(0x7ff8000000000000LL);
       }
       bad |= cell_bad;
     }

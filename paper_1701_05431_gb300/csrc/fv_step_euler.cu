@@ -45,6 +45,8 @@ void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT_INPL(double, 0, 1, 16, 4, 3, -4, "euler f64 v1 ty16 w4 b3 async4 inplace");
   FV_VARIANT_INPL(float, 1, 4, 32, 4, 3, -4, "euler f32 v4 ty32 w4 b3 async4 inplace");
   FV_VARIANT_INPL(float, 1, 2, 16, 4, 4, -6, "euler f32 v2 ty16 w4 b4 async6 inplace");
+  FV_VARIANT_INPL(float, 1, 2, 32, 4, 4, -6, "euler f32 v2 ty32 w4 b4 async6 inplace");
+  FV_VARIANT_INPL(float, 1, 4, 64, 4, 3, -4, "euler f32 v4 ty64 w4 b3 async4 inplace");
   FV_VARIANT_INPL(BF, 2, 4, 32, 4, 3, -4, "euler bf16 v4 ty32 w4 b3 async4 inplace");
   FV_VARIANT_INPL(BF, 2, 2, 16, 4, 4, -6, "euler bf16 v2 ty16 w4 b4 async6 inplace");
   FV_VARIANT(double, 0, 1, 64, 4, 1, 0, "euler f64 v1 ty64 w4");

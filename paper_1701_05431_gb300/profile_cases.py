@@ -11,8 +11,9 @@ C ABI and advances the given number of time steps once; nothing is timed.
 `--tune K` (K >= 2) forces kernel candidate K - 2, so that a capture sees a
 known kernel.  `sweep` times every compiled candidate in turn on one workload
 (c3: Euler 8192^2 smooth periodic; c2: four-quadrant 2048^2; c4: 512 batched
-instances; c3tb: the c3 grid in fixed-dt mode with two-step passes) with CUDA
-events and prints one JSON line per candidate.
+instances; c3tb: the c3 grid in fixed-dt mode with two-step passes;
+c3inplace: the c3 grid with one state buffer) with CUDA events and prints one
+JSON line per candidate.
 """
 from __future__ import annotations
 
@@ -116,6 +117,23 @@ def sweep(workload: str, precision: str, steps: int) -> None:
                                   "cell_updates_per_s": ncells * steps / sec}), flush=True)
             k += 1
         return
+    if workload == "c3inplace":
+        # one state buffer, every in-place candidate
+        prim, d = wl.smooth_periodic(8192, dtype=np.float32)
+        dev = _device(prim)
+        k = 0
+        while True:
+            with fvlib.Solver(d, precision, stream=stream, tune=2 + k) as s:
+                try:
+                    s.set_inplace(True)
+                except fvlib.FvError:
+                    break
+                s.set_state(dev, primitive=True)
+                sec = _timed(lambda: s.run(steps))
+                print(json.dumps({"workload": workload, "precision": precision, "kernel": s.kernel_info()[1],
+                                  "cell_updates_per_s": d["nx"] * d["ny"] * steps / sec}), flush=True)
+            k += 1
+        return
     if workload == "c3tb":
         # two-step passes, fixed dt = 0.4 min(dx, dy) / lmax(W^0), every two-step candidate
         prim, d = wl.smooth_periodic(8192, dtype=np.float32)
@@ -152,7 +170,7 @@ def sweep(workload: str, precision: str, steps: int) -> None:
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("case", choices=["step", "batch", "spray", "sweep"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c3tb"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c3tb", "c3inplace"])
     ap.add_argument("--system", default="euler", choices=["euler", "advection"])
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--n", type=int, default=4096)

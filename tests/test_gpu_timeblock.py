@@ -105,7 +105,9 @@ def test_switching_and_split_runs():
     with f.Solver(d, "f32") as s:
         s.set_state(prim, primitive=True)
         s.run(5)
+        assert s.two_step_kernel() is None
         s.set_time_blocking(2)
+        assert "tb2" in s.two_step_kernel()
         s.run(7)
         s.run(10)
         snap = np.empty((4, 90, 150), dtype=np.float32)
