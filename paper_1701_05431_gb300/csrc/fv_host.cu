@@ -66,7 +66,8 @@ struct fv_ctx {
   size_t staging_bytes = 0;
   double *partials = nullptr;
   double *d_totals = nullptr;
-  double *lamw = nullptr;        // spray: multipliers of the last two solves (8 planes)
+  double *lamw = nullptr;        // spray: multipliers of the last three solves (12 planes)
+  double *ecache = nullptr;      // spray: exponentials of the last solve (Q planes)
   double *nodes = nullptr;       // spray: quadrature table
   int spray_Q = 0;
   int src_grid = 0;
@@ -310,6 +311,7 @@ static fv_status launch_step(fv_ctx *c, cudaStream_t s) {
     L.buf1 = c->buf[1];
     L.ctrl = c->ctrl;
     L.lamw = c->lamw;
+    L.ecache = c->ecache;
     L.nodes = c->nodes;
     L.nx = c->cfg.nx;
     L.ny = c->cfg.ny;
@@ -455,7 +457,9 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     if ((e = cudaMalloc(&c->nodes, sizeof(double) * tab.size())) != cudaSuccess) return bail(e, "cudaMalloc(nodes)");
     if ((e = cudaMemcpy(c->nodes, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(e, "cudaMemcpy(nodes)");
-    if ((e = cudaMalloc(&c->lamw, sizeof(double) * 8 * c->plane)) != cudaSuccess) return bail(e, "cudaMalloc(lamw)");
+    if ((e = cudaMalloc(&c->lamw, sizeof(double) * 12 * c->plane)) != cudaSuccess) return bail(e, "cudaMalloc(lamw)");
+    if ((e = cudaMalloc(&c->ecache, sizeof(double) * Q * c->plane)) != cudaSuccess)
+      return bail(e, "cudaMalloc(exponential cache)");
     c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, Q, c->sms);
   }
   int prec = cfg->precision;  // 0 f64, 1 f32, 2 bf16 storage
@@ -503,6 +507,7 @@ extern "C" void fv_destroy(fv_ctx *c) {
   if (c->partials) cudaFree(c->partials);
   if (c->d_totals) cudaFree(c->d_totals);
   if (c->lamw) cudaFree(c->lamw);
+  if (c->ecache) cudaFree(c->ecache);
   if (c->nodes) cudaFree(c->nodes);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
@@ -559,7 +564,7 @@ static fv_status seed(fv_ctx *c, long long step, double t, unsigned cur) {
   *c->h_ctrl = h;
   FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
   if (c->lamw)  // all-ones bytes are NaNs: every cell starts its Newton solve cold
-    FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 8 * c->plane, c->stream));
+    FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 12 * c->plane, c->stream));
   double p0 = c->cfg.params[0], p1 = c->cfg.params[1];
   if (c->cfg.system == FV_EULER) p1 = c->cfg.params[0] - 1.0;
   FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision, c->buf[cur],

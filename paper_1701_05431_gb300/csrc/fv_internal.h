@@ -57,6 +57,7 @@ struct SourceLaunch {
   void *buf0, *buf1;
   Ctrl *ctrl;
   double *lamw;
+  double *ecache;        // Q planes: the exponentials of the last solve (nullable)
   const double *nodes;
   int nx, ny;
   long long pitch, plane;

@@ -10,16 +10,19 @@
 // Hankel-type moment matrices loses too many digits); the moments of a trial
 // density are Gauss-Legendre sums in x = sqrt(S) whose nodes and
 // pre-multiplied weights sit in shared memory.  The multipliers of each cell
-// are kept between steps (warm start), those of the two last steps, and the
-// solve starts from their linear extrapolation: the moments move smoothly,
-// by O(dt) per step, so Newton usually needs two or three moment evaluations
-// instead of eight.
+// are kept between steps (warm start), those of the three last steps, and
+// the solve starts from their quadratic extrapolation: the moments move
+// smoothly, by O(dt) per step, so Newton usually needs two moment
+// evaluations instead of eight.
 // Only the first evaluation of a solve computes the Q exponentials
 // e_q = exp(-p(x_q)) (p the multipliers' polynomial); they stay in shared
-// memory, and after a Newton step d with sum |d_k| <= 2^-10 the next
-// evaluation multiplies them by exp(-p_d(x_q)), |p_d| <= 2^-10, from its
-// Taylor polynomial of degree 6 (truncation < 1e-24 relative), which costs
-// six FMAs instead of an exponential per node.
+// memory, and after a Newton step d with sum |d_k| <= 2^-6 the next
+// evaluation multiplies them by exp(-p_d(x_q)), |p_d| <= 2^-6, from its
+// Taylor polynomial of degree 10 (truncation < 4e-28 relative), which costs
+// ten FMAs instead of an exponential per node.  The exponentials of each
+// cell's last solve are kept between steps too (Q planes), so that even the
+// first evaluation of a solve is such an update when the start is close to
+// the last solution; every 32 steps they are computed afresh.
 // After the update the kernel reduces lmax(W^{n+1}) and closes the step.
 #include <cuda_runtime.h>
 
@@ -38,7 +41,8 @@ template <class R> struct SourceArgs {
   R *buf0;
   R *buf1;
   Ctrl *ctrl;
-  double *lamw;          // 8 planes of ny x pitch: multipliers of the last two solves
+  double *lamw;          // 12 planes of ny x pitch: multipliers of the last three solves
+  double *ecache;        // Q planes of ny x pitch: exp(-p(x_q)) at the last solve's multipliers
   const double *nodes;   // Q x kNodeStride
   int nx, ny;
   long long pitch, plane;
@@ -67,10 +71,15 @@ static __device__ __forceinline__ void me_moments(const double *nd, int Q, const
   }
 }
 
-// exp(-t) for |t| <= 2^-10: Taylor polynomial of degree 6 in Horner form.
+// exp(-t) for |t| <= 2^-6: Taylor polynomial of degree 10 in Horner form
+// (truncation below |t|^11 / 11! < 4e-28).
 static __device__ __forceinline__ double exp_neg_small(double t) {
   const double u = -t;
-  double p = 1.0 / 720.0;
+  double p = 1.0 / 3628800.0;
+  p = fma(p, u, 1.0 / 362880.0);
+  p = fma(p, u, 1.0 / 40320.0);
+  p = fma(p, u, 1.0 / 5040.0);
+  p = fma(p, u, 1.0 / 720.0);
   p = fma(p, u, 1.0 / 120.0);
   p = fma(p, u, 1.0 / 24.0);
   p = fma(p, u, 1.0 / 6.0);
@@ -81,7 +90,7 @@ static __device__ __forceinline__ double exp_neg_small(double t) {
 
 // The moments after the multipliers moved by d, from the cached e_q of the
 // previous multipliers: e_q <- e_q exp(-(d0 + d1 x + d2 x^2 + d3 x^3)).
-// Requires |d0| + |d1| + |d2| + |d3| <= 2^-10.
+// Requires |d0| + |d1| + |d2| + |d3| <= 2^-6.
 static __device__ __forceinline__ void me_moments_step(const double *nd, int Q, const double (&d)[4],
                                                        double (&M)[8], double *e, int es) {
 #pragma unroll
@@ -98,7 +107,7 @@ static __device__ __forceinline__ void me_moments_step(const double *nd, int Q, 
   }
 }
 
-constexpr double kIncrementalStep = 0x1p-10;
+constexpr double kIncrementalStep = 0x1p-6;
 
 // Cholesky solve of the 4 x 4 SPD system H d = r; false if H is not SPD.
 static __device__ __forceinline__ bool spd_solve4(const double (&M)[8], const double (&r)[4],
@@ -148,13 +157,14 @@ static __device__ __forceinline__ bool realizable(const double (&c)[4]) {
 // Maximum-entropy reconstruction: returns false when Newton fails.  e is
 // the thread's exponential cache (Q values, stride es).
 static __device__ bool maxent(const double *nd, int Q, double tol, const double (&m)[4], double (&lam)[4],
-                              double &n0, double &mmh, double *e, int es) {
+                              double &n0, double &mmh, double *e, int es, int have0, const double (&d0)[4]) {
   double M[8];
   bool ok = false;
   // how the moments of the current multipliers are obtained: 0 from scratch,
-  // 1 from the cache and the last full Newton step `d`, 2 already in M
-  int have = 0;
-  double d[4] = {0.0, 0.0, 0.0, 0.0};
+  // 1 from the cache and the last full Newton step `d` (on entry: the cache
+  // holds the exponentials at lam - d0 if have0 == 1), 2 already in M
+  int have = have0;
+  double d[4] = {d0[0], d0[1], d0[2], d0[3]};
   for (int it = 0; it < 100; ++it) {
     if (have == 0) me_moments(nd, Q, lam, M, e, es);
     else if (have == 1) me_moments_step(nd, Q, d, M, e, es);
@@ -208,7 +218,7 @@ static __device__ bool maxent(const double *nd, int Q, double tol, const double 
 }
 
 template <class R>
-__global__ void __launch_bounds__(kSrcThreads)
+__global__ void __launch_bounds__(kSrcThreads, 3)
 fv_spray_source_kernel(const SourceArgs<R> a) {
   __shared__ double s_lam[kSrcWarps];
   __shared__ int s_bad[kSrcWarps];
@@ -234,29 +244,55 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
       for (int v = 0; v < 6; ++v) w[v] = (double)W[v * a.plane + o];
       const double m[4] = {w[0], w[1], w[2], w[3]};
       bool cell_bad = !realizable(m);
-      // start from the multipliers of the last solve, extrapolated linearly
-      // in time from the two last solves when both exist (the moments move
-      // smoothly from step to step, so the start is closer by an order of dt)
-      double lam[4], lam_prev[4];
-      const double warm0 = a.lamw[o], prev0 = a.lamw[4 * a.plane + o];
+      // start from the multipliers of the last solve, extrapolated in time
+      // from the last two or three solves that exist (the moments move
+      // smoothly from step to step: a quadratic extrapolation lands within
+      // O(dt^3) of the solution, close enough for one Newton step)
+      double lam[4], lam_prev[4], lam_prev2[4];
+      const double warm0 = a.lamw[o], prev0 = a.lamw[4 * a.plane + o], prev20 = a.lamw[8 * a.plane + o];
       if (warm0 == warm0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           lam_prev[q] = a.lamw[q * a.plane + o];
+          lam_prev2[q] = a.lamw[(4 + q) * a.plane + o];
           lam[q] = lam_prev[q];
         }
-        if (prev0 == prev0) {
+        if (prev0 == prev0 && prev20 == prev20) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) lam[q] = 2.0 * lam_prev[q] - a.lamw[(4 + q) * a.plane + o];
+          for (int q = 0; q < 4; ++q)
+            lam[q] = 3.0 * (lam_prev[q] - lam_prev2[q]) + a.lamw[(8 + q) * a.plane + o];
+        } else if (prev0 == prev0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) lam[q] = 2.0 * lam_prev[q] - lam_prev2[q];
         }
       } else {
         lam[0] = -log(m[0]);
         lam[1] = lam[2] = lam[3] = 0.0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) lam_prev[q] = __longlong_as_double(0x7ff8000000000000LL);
+        for (int q = 0; q < 4; ++q) lam_prev[q] = lam_prev2[q] = __longlong_as_double(0x7ff8000000000000LL);
+      }
+      // the first evaluation updates the last solve's exponentials when the
+      // start moved little from its multipliers (a full evaluation every 32
+      // steps bounds the roundings the updates accumulate)
+      int have0 = 0;
+      double d0[4] = {0.0, 0.0, 0.0, 0.0};
+      if (a.ecache && warm0 == warm0 && (st.step & 31) != 0) {
+        double moved = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          d0[q] = lam[q] - lam_prev[q];
+          moved += fabs(d0[q]);
+        }
+        if (moved <= kIncrementalStep) {
+          for (int q = 0; q < a.Q; ++q) s_exp[q * kSrcThreads + threadIdx.x] = a.ecache[q * a.plane + o];
+          have0 = 1;
+        }
       }
       double n0 = 0.0, mmh = 0.0;
-      if (!cell_bad) cell_bad = !maxent(s_nodes, a.Q, a.tol, m, lam, n0, mmh, s_exp + threadIdx.x, kSrcThreads);
+      if (!cell_bad)
+        cell_bad = !maxent(s_nodes, a.Q, a.tol, m, lam, n0, mmh, s_exp + threadIdx.x, kSrcThreads, have0, d0);
+      if (!cell_bad && a.ecache)
+        for (int q = 0; q < a.Q; ++q) a.ecache[q * a.plane + o] = s_exp[q * kSrcThreads + threadIdx.x];
       if (!cell_bad) {
         const double K = a.K;
         const double u = w[4] / w[2], v = w[5] / w[2];
@@ -291,12 +327,14 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
         lmax = fmax(lmax, (double)l);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+          a.lamw[(8 + q) * a.plane + o] = lam_prev2[q];
           a.lamw[(4 + q) * a.plane + o] = lam_prev[q];
           a.lamw[q * a.plane + o] = lam[q];
         }
       } else {
         a.lamw[o] = __longlong_as_double(0x7ff8000000000000LL);
         a.lamw[4 * a.plane + o] = __longlong_as_double(0x7ff8000000000000LL);
+        a.lamw[8 * a.plane + o] = __longlong_as_double(0x7ff8000000000000LL);
       }
       bad |= cell_bad;
     }
@@ -311,6 +349,7 @@ static SourceArgs<R> make_source_args(const SourceLaunch &L) {
   a.buf1 = (R *)L.buf1;
   a.ctrl = L.ctrl;
   a.lamw = L.lamw;
+  a.ecache = L.ecache;
   a.nodes = L.nodes;
   a.nx = L.nx;
   a.ny = L.ny;
