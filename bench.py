@@ -177,9 +177,35 @@ def cpu_baseline_run(name, d, prim, sample_steps=None, seconds_target=15.0):
     t = time.perf_counter()
     r = oracle.run(P, r.W, steps)
     el = time.perf_counter() - t
-    return {"value": ncell * steps / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
-            "sample": f"{name}: full {d['nx']}x{d['ny']} grid, {steps} FP64 steps (plain mode) after one "
-                      f"warm-up step, {el:.1f} s"}
+    out = {"value": ncell * steps / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+           "sample": f"{name}: full {d['nx']}x{d['ny']} grid, {steps} FP64 steps (plain mode) after one "
+                     f"warm-up step, {el:.1f} s"}
+    # the same oracle on one thread, one step of a 4096^2 grid of the same data recipe
+    if ncell > 4096 * 4096:
+        prim1, d1 = wl.smooth_periodic(4096)
+        P1 = oracle_problem(d1)
+        W1 = oracle.prim_to_cons(P1, prim1)
+        t = time.perf_counter()
+        oracle.run(P1, W1, 1, nthreads=1)
+        el1 = time.perf_counter() - t
+        out["single_thread"] = {"value": 4096 * 4096 / el1, "unit": "cell-updates/s", "cores": 1,
+                                "sample": f"one FP64 step of a 4096x4096 grid of the same recipe, {el1:.1f} s"}
+    return out
+
+
+def oracle_sample(d, prim, steps, what):
+    """Oracle cell-updates/s on the host cores for `steps` steps of one
+    configuration (input prepared outside the timed region)."""
+    import oracle
+    from tests.helpers import oracle_problem
+    oracle.build()
+    P = oracle_problem(d)
+    W = oracle.prim_to_cons(P, prim)
+    t = time.perf_counter()
+    r = oracle.run(P, W, steps)
+    el = time.perf_counter() - t
+    return {"value": d["nx"] * d["ny"] * steps / el, "unit": "cell-updates/s", "cores": oracle.max_threads(),
+            "status": int(r.status), "sample": f"{what}: {steps} FP64 steps of {d['nx']}x{d['ny']}, {el:.2f} s"}
 
 
 def run_reference(args):
@@ -223,7 +249,7 @@ def run_reference(args):
     return 0
 
 
-def secondary_workloads(fvlib, torch, sptr, local, hbm):
+def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
     """The other configurations of the hot path, one or two timed jobs each
     (device-resident inputs, CUDA events around the run calls)."""
     out = {}
@@ -248,6 +274,8 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
         sec = timed(lambda: s.run(100), 5)
         out["c1_advection_128_f64"] = {"cell_updates_per_s": 128 * 128 * 100 / sec, "ms_per_job": sec * 1e3,
                                        "kernel": s.kernel_info()[1]}
+    if oracle_too:
+        out["c1_advection_128_f64"]["oracle"] = oracle_sample(d, prim, 100, "the whole job")
     # C2: four-quadrant Euler 2048^2, 8x8 subdomains, FP64, 500 steps (and FP32)
     prim, d = wl.four_quadrant(2048, npart=8)
     pd = torch.from_numpy(prim).to(f"cuda:{local}")
@@ -262,10 +290,22 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
                 "cell_updates_per_s": 2048 * 2048 * 500 / sec, "ms_per_job": sec * 1e3,
                 "hbm_gbs_algorithmic": nb / sec / 1e9, "kernel": s.kernel_info()[1],
                 "note": "job = set_state from device + 500 steps; 134 MB/268 MB state, close to L2 size"}
+    if oracle_too:
+        out["c2_four_quadrant_2048_f64"]["oracle"] = oracle_sample(d, prim, 5, "a sample")
     del pd
     # C4: 512 batched four-quadrant instances, FP32, 200 steps in one persistent launch
     insts = wl.batched_quadrants(512)
     ncells = sum(dd["nx"] * dd["ny"] for _, _, dd in insts)
+    c4_oracle = None
+    if oracle_too:
+        # eight of the instances, 20 steps each
+        vals, cells, secs = [], 0, 0.0
+        for _, pr, dd in insts[:8]:
+            o = oracle_sample(dd, pr, 20, "instance")
+            cells += dd["nx"] * dd["ny"] * 20
+            secs += dd["nx"] * dd["ny"] * 20 / o["value"]
+        c4_oracle = {"value": cells / secs, "unit": "cell-updates/s", "cores": o["cores"],
+                     "sample": f"the first 8 of the 512 instances, 20 FP64 steps each, {secs:.2f} s"}
     with fvlib.Batch([dd for _, _, dd in insts], "f32", stream=sptr, tune=1) as b:
         for k, (_, pr, _) in enumerate(insts):
             b.set_state(k, pr, primitive=True)
@@ -277,6 +317,8 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
                                      "hbm_frac": nb / sec / 1e9 / hbm, "kernel": b.kernel_info()[1],
                                      "kernel_choice": "autotuned (one timed step per candidate before the first run)",
                                      "launches_per_job": 1}
+        if c4_oracle:
+            out["c4_batched_512_f32"]["oracle"] = c4_oracle
     # The paper's fixed dt (per instance: 0.4 min(dx, dy) / lmax(W^0)) on the
     # same 512 instances, step-gated and with device dataflow (neighbour
     # dependencies, no barrier per step); and one 8192^2 grid as a batch of one
@@ -373,6 +415,8 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm):
                 "cell_updates_per_s": 2048 * 2048 * 200 / sec, "ms_per_job": sec * 1e3,
                 "kernel": s.kernel_info()[1],
                 "bound": "fp64 pipe (maximum-entropy Newton in FP64 in both precisions)"}
+    if oracle_too:
+        out["c5_spray_2048_f64"]["oracle"] = oracle_sample(d, prim, 2, "a sample (cold Newton starts)")
     del pd
     return out
 
@@ -558,7 +602,8 @@ def main():
         out["accuracy_vs_oracle"] = dict(acc, samples=int(len(g["flat_index"])), steps=int(g["steps"]))
 
     if not args.no_extra and args.workload == "c3":
-        out["other_workloads"] = secondary_workloads(fvlib, torch, sptr, local, hbm)
+        out["other_workloads"] = secondary_workloads(fvlib, torch, sptr, local, hbm,
+                                                     oracle_too=(rank == 0 and not args.no_cpu_baseline and ws == 1))
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline_run(args.workload, d, prim)
