@@ -57,6 +57,9 @@ WORKLOADS = {
            "advection 128x128 a=(1,0.5) periodic, CFL 0.5, 100 steps"),
 }
 
+# the bench's metric, the same string on both arms
+METRIC = "cell-updates/s (FP32-bulk; FP64 plain beside it) and HBM GB/s"
+
 BYTES_PER_CELL = {"advection": 1, "euler": 4, "spray": 6}  # nvar
 
 
@@ -159,6 +162,17 @@ def dist_env():
     return ws, rank, local
 
 
+def cpu_model() -> str:
+    """The host CPU as lscpu names it (model name and core count)."""
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        info = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l)
+        name = (info.get("Model name") or info.get("Vendor ID") or "").strip()
+        return f"{name}, {os.cpu_count()} logical CPUs".strip(", ")
+    except Exception:
+        return f"{os.cpu_count()} logical CPUs"
+
+
 def cpu_baseline_run(name, d, prim, sample_steps=None, seconds_target=15.0):
     """Time the FP64 oracle, as it stands, on the host cores on a bounded
     sample of the workload (a few steps on the full grid)."""
@@ -178,6 +192,7 @@ def cpu_baseline_run(name, d, prim, sample_steps=None, seconds_target=15.0):
     r = oracle.run(P, r.W, steps)
     el = time.perf_counter() - t
     out = {"value": ncell * steps / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+           "cpu": cpu_model(),
            "sample": f"{name}: full {d['nx']}x{d['ny']} grid, {steps} FP64 steps (plain mode) after one "
                      f"warm-up step, {el:.1f} s"}
     # the same oracle on one thread, one step of a 4096^2 grid of the same data recipe
@@ -235,12 +250,12 @@ def run_reference(args):
         W = r.W
     el = sum(times)
     value = ncell * per * args.steps / el
-    line = {"impl": "reference", "metric": "cell-updates/s (FP64 CPU oracle)", "value": value,
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "sample_steps_per_bench_step": per},
-            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.max_threads(),
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.max_threads(), "cpu": cpu_model(),
                              "kind": "oracle",
                              "sample": f"{per} FV steps of the full {d['nx']}x{d['ny']} grid per bench step"},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
@@ -501,7 +516,7 @@ def main():
     avg_launch_s = ms32 / 1e3 / launches
     achieved32 = algo_bytes_32 / avg_launch_s / 1e9
 
-    out = {"metric": "cell-updates/s (FP32-bulk; FP64 plain beside it) and HBM GB/s",
+    out = {"metric": METRIC,
            "value": value32, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
