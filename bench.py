@@ -527,7 +527,7 @@ def main():
                         "frac": achieved32 / hbm,
                         "traffic": (None if measured_traffic_per_cell(kinfo32) is None
                                     else measured_traffic_per_cell(kinfo32) * ncell),
-                        "traffic_source": "ncu dram__bytes_read+write of this kernel on 4096^2, scaled by cells",
+                        "traffic_source": "ncu dram__bytes_read+write of one launch of this kernel on the 8192^2 workload",
                         "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                         "algorithmic_bytes_per_launch": algo_bytes_32,
                         "avg_launch_us": avg_launch_s * 1e6},
