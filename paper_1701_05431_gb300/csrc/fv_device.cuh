@@ -45,6 +45,7 @@ template <class R> struct Ops;
 //   P        type of parameters, boundary states and wave-speed maxima
 //   K        cells packed in one A (1, or 2 for F2)
 //   add/sub/mul/fma/rcp/sqrt/abs/max/neg   per component, explicitly rounded
+//                         (max is only taken of non-negative values: speeds)
 //   splat(s), pack(p), unpack(x, p)        conversions to and from storage
 //   shfl_up/shfl_down                      warp shuffles of whole values
 //   shift_in(prev, cur)   the values one cell to the west of `cur`, given the
@@ -66,7 +67,14 @@ template <> struct Ops<double> {
   static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
   static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
   static __device__ __forceinline__ double abs(double a) { return fabs(a); }
-  static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
+  // The FP64 pipe bounds the FP64 kernels, so comparisons run on the integer
+  // pipe: non-negative doubles order like their bit patterns read as signed
+  // 64-bit integers (a NaN operand with a clear sign bit is returned, where
+  // fmax would drop it; a NaN speed flags the step either way).
+  static __device__ __forceinline__ double max(double a, double b) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return __longlong_as_double(x > y ? x : y);
+  }
   static __device__ __forceinline__ double neg(double a) { return -a; }
   static __device__ __forceinline__ double splat(double s) { return s; }
   static __device__ __forceinline__ double pack(const double *p) { return p[0]; }
@@ -75,8 +83,16 @@ template <> struct Ops<double> {
   static __device__ __forceinline__ double shfl_down(double x, int d) { return __shfl_down_sync(0xffffffffu, x, d); }
   static __device__ __forceinline__ double shift_in(double prev, double) { return prev; }
   static __device__ __forceinline__ double shift_out(double, double next) { return next; }
-  static __device__ __forceinline__ unsigned not_pos(double x) { return (x > 0.0) ? 0u : 1u; }
-  static __device__ __forceinline__ unsigned not_fin(double x) { return (fabs(x) <= 3.0e38) ? 0u : 1u; }
+  // x > 0 exactly as the FP64 comparison decides it (false for NaN, -0 and
+  // +0): the bit pattern minus one lies below that of +Inf
+  static __device__ __forceinline__ unsigned not_pos(double x) {
+    return ((unsigned long long)__double_as_longlong(x) - 1ull < 0x7ff0000000000000ull) ? 0u : 1u;
+  }
+  // |x| <= 3e38 on the magnitude bits (NaN and Inf lie above)
+  static __device__ __forceinline__ unsigned not_fin(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) <=
+                   (unsigned long long)__double_as_longlong(3.0e38) ? 0u : 1u;
+  }
   static __device__ __forceinline__ double hmax(double x, unsigned mask) { return (mask & 1u) ? x : 0.0; }
 };
 
