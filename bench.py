@@ -569,20 +569,26 @@ def main():
         P0 = np.ascontiguousarray(prim.astype(np.float32))
         h_in = torch.from_numpy(P0).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
-        s.set_state(h_in, primitive=True)
+        # one untimed job through the same calls (allocates the side buffers)
+        s.prefetch_state(h_in, primitive=True)
+        s.set_state_prefetched()
         s.run(nsteps_job)
-        s.get_state(h_out)
-        k = max(1, min(args.steps, 3))
-        # each job: inputs copied in from pinned host memory, 100 steps, the
-        # result copied out; the copy out is an asynchronous snapshot, so it
-        # overlaps the next job (the last one is waited for inside the region)
         s.snapshot(h_out)
         s.snapshot_wait()
+        k = max(2, min(args.steps, 8))
+        # each job: its input copied in from pinned host memory, nsteps_job
+        # steps, its result copied out to pinned host memory.  The copy in of
+        # job j+1 (fv_prefetch_state) and the copy out of job j (fv_snapshot)
+        # run on side streams while job j+1's steps run; the first copy in and
+        # the last copy out are inside the region and overlap nothing.
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(k):
-            s.set_state(h_in, primitive=True)
+        s.prefetch_state(h_in, primitive=True)
+        for j in range(k):
+            s.set_state_prefetched()
+            if j + 1 < k:
+                s.prefetch_state(h_in, primitive=True)
             s.run(nsteps_job)
             s.snapshot(h_out)
         s.snapshot_wait()
@@ -593,7 +599,8 @@ def main():
         out["e2e"] = {"value": ncell * nsteps_job * k * ws / wall, "unit": "cell-updates/s",
                       "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4),
                       "wall_s": wall, "steps": k,
-                      "path": "fv_set_state(pinned host f32 primitive) + fv_run + fv_snapshot(pinned host f32, "
+                      "path": "fv_prefetch_state(pinned host f32 primitive, asynchronous, overlapping the previous "
+                              "job) + fv_set_state_prefetched + fv_run + fv_snapshot(pinned host f32, "
                               "asynchronous, overlapping the next job) + fv_snapshot_wait; host wall clock"}
         out["e2e"]["gpu_launches"] = k * (nsteps_job + 3)
 

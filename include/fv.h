@@ -195,6 +195,25 @@ fv_status fv_snapshot(fv_ctx *ctx, void *dst, int dst_dtype);
  * (FV_OK at once if none is pending). */
 fv_status fv_snapshot_wait(fv_ctx *ctx);
 
+/* Asynchronous input, the counterpart of fv_snapshot: queues on a side
+ * stream of the context the copy of a state (fv_set_state's src layout,
+ * nVar x Ny x Nx values of src_dtype, FV_F64 or FV_F32, conserved or
+ * primitive per layout) from caller-owned HOST memory into a device buffer
+ * owned by the context, and returns without waiting; with pinned memory the
+ * copy runs while the steps already queued go on (pageable memory: the call
+ * returns after the copy).  src must stay valid and unchanged until the
+ * state is loaded by fv_set_state_prefetched.  A prefetch replaces one not
+ * yet loaded; it waits on the device until the previous load has read the
+ * buffer.  Errors: FV_ERR_INVALID_ARG (NULL src, bad dtype or layout),
+ * FV_ERR_OOM, FV_ERR_CUDA. */
+fv_status fv_prefetch_state(fv_ctx *ctx, const void *src, int src_dtype, int layout);
+
+/* fv_set_state from the last fv_prefetch_state: the context's stream waits
+ * on the device for the copy, then the state is loaded at t = 0, step 0 and
+ * checked exactly as by fv_set_state (same results bit for bit, same errors;
+ * synchronises the stream).  FV_ERR_STATE when no prefetch is pending. */
+fv_status fv_set_state_prefetched(fv_ctx *ctx);
+
 /* Per-variable totals sum_ij W_v dx dy of the current state (nVar doubles
  * into host memory), FP64 Neumaier-compensated block sums combined in a
  * fixed order (deterministic).  Synchronises the stream. */

@@ -20,7 +20,8 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(
   return __double2bfloat16(x);
 }
 
-// One thread per cell.  src is contiguous nvar x ny x nx; state is pitched.
+// Threads stride along a row, blocks along y over rows (no integer division
+// per cell).  src is contiguous nvar x ny x nx; state is pitched.
 // Primitive -> conserved, in FP64 and in the same operation order as the
 // definition: rho E = p/(gamma - 1) + rho (u u + v v)/2; momenta = rho u, rho v
 // (Euler) or m1 u, m1 v (spray).
@@ -29,9 +30,9 @@ __global__ void load_state_kernel(int system, const S *__restrict__ src, int pri
                                   R *__restrict__ state, int nx, int ny, long long pitch,
                                   long long plane, double gamma) {
   const long long ncell = (long long)nx * ny;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(k / nx), i = (int)(k % nx);
+  for (int j = blockIdx.y; j < ny; j += gridDim.y)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+    const long long k = (long long)j * nx + i;
     const long long o = (long long)j * pitch + i;
     if (system == kAdvection) {
       state[o] = from_double<R>(rd(src, k));
@@ -43,7 +44,8 @@ __global__ void load_state_kernel(int system, const S *__restrict__ src, int pri
         w1 = __dmul_rn(rho, u);
         w2 = __dmul_rn(rho, v);
         const double q = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
-        w3 = __dadd_rn(__ddiv_rn(p, __dsub_rn(gamma, 1.0)), __ddiv_rn(__dmul_rn(rho, q), 2.0));
+        // (halving is exact: the product by 0.5 is the quotient by 2)
+        w3 = __dadd_rn(__ddiv_rn(p, __dsub_rn(gamma, 1.0)), __dmul_rn(__dmul_rn(rho, q), 0.5));
       }
       state[o] = from_double<R>(w0);
       state[plane + o] = from_double<R>(w1);
@@ -63,18 +65,23 @@ __global__ void load_state_kernel(int system, const S *__restrict__ src, int pri
   }
 }
 
-static int grid_for(long long n, int threads) {
-  long long b = (n + threads - 1) / threads;
-  if (b > 152 * 32) b = 152 * 32;
-  if (b < 1) b = 1;
-  return (int)b;
+// Blocks of `threads` along x (a row) and over rows along y, about 32 per SM
+// of a 152-SM GPU in all.
+static dim3 grid_for(int nx, int ny, int threads) {
+  int gx = (nx + threads - 1) / threads;
+  if (gx > 64) gx = 64;
+  if (gx < 1) gx = 1;
+  int gy = 152 * 32 / gx;
+  if (gy > ny) gy = ny;
+  if (gy < 1) gy = 1;
+  return dim3((unsigned)gx, (unsigned)gy);
 }
 
 cudaError_t launch_load_state(int system, int prec, const void *src, int src_f32, int primitive,
                               void *state, int nx, int ny, long long pitch, long long plane,
                               double gamma, cudaStream_t s) {
   const int th = 256;
-  const int g = grid_for((long long)nx * ny, th);
+  const dim3 g = grid_for(nx, ny, th);
   if (prec == 0) {
     if (src_f32)
       load_state_kernel<float, double><<<g, th, 0, s>>>(system, (const float *)src, primitive,
@@ -105,9 +112,9 @@ template <class R, class D>
 __global__ void store_state_kernel(int nvar, const R *__restrict__ state, D *__restrict__ dst, int nx,
                                    int ny, long long pitch, long long plane) {
   const long long ncell = (long long)nx * ny;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(k / nx), i = (int)(k % nx);
+  for (int j = blockIdx.y; j < ny; j += gridDim.y)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+    const long long k = (long long)j * nx + i;
     const long long o = (long long)j * pitch + i;
     for (int v = 0; v < nvar; ++v) dst[v * ncell + k] = (D)to_double(state[v * plane + o]);
   }
@@ -116,7 +123,7 @@ __global__ void store_state_kernel(int nvar, const R *__restrict__ state, D *__r
 cudaError_t launch_store_state(int prec, int nvar, const void *state, void *dst, int dst_f32, int nx,
                                int ny, long long pitch, long long plane, cudaStream_t s) {
   const int th = 256;
-  const int g = grid_for((long long)nx * ny, th);
+  const dim3 g = grid_for(nx, ny, th);
   if (prec == 0) {
     if (dst_f32)
       store_state_kernel<double, float><<<g, th, 0, s>>>(nvar, (const double *)state, (float *)dst, nx,
@@ -150,12 +157,10 @@ __global__ void seed_lambda_kernel(const typename Ops<A>::S *__restrict__ state,
                                    long long plane, SysParams<typename Ops<A>::P> Pp, Ctrl *ctrl, int slot) {
   constexpr int NV = Sys::NV;
   const SysParams<A> P = splat_params<A>(Pp);
-  const long long ncell = (long long)nx * ny;
-  double l = 0.0;
+  typename Ops<A>::P l = 0;
   bool bad = false;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncell;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(k / nx), i = (int)(k % nx);
+  for (int j = blockIdx.y; j < ny; j += gridDim.y)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
     const long long o = (long long)j * pitch + i;
     A W[NV];
 #pragma unroll
@@ -163,13 +168,13 @@ __global__ void seed_lambda_kernel(const typename Ops<A>::S *__restrict__ state,
     unsigned b;
     const A lc = Sys::lambda(W, P, b);
     bad |= b != 0u;
-    l = fmax(l, (double)Ops<A>::hmax(lc, 1u));
+    l = fmax(l, Ops<A>::hmax(lc, 1u));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
   const int anybad = __any_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
-    if (l > 0.0) atomicMax(&ctrl->lam[slot], lam_bits(l));
+    if (l > 0) atomicMax(&ctrl->lam[slot], lam_bits((double)l));
     if (anybad) atomicOr(&ctrl->err_pending, kErrNonphysical);
   }
 }
@@ -178,7 +183,7 @@ cudaError_t launch_seed_lambda(int system, int prec, const void *state, int nx, 
                                long long pitch, long long plane, double p0, double p1, Ctrl *ctrl,
                                int slot, cudaStream_t s) {
   const int th = 256;
-  const int g = grid_for((long long)nx * ny, th);
+  const dim3 g = grid_for(nx, ny, th);
   if (prec == 0) {
     SysParams<double> P{p0, p1};
     const double *st = (const double *)state;

@@ -79,6 +79,14 @@ struct fv_ctx {
   cudaStream_t snap_stream = nullptr;
   cudaEvent_t snap_ready = nullptr, snap_done = nullptr;
   bool snap_pending = false;
+  // asynchronous input prefetch: device buffer, side stream, events
+  void *pre_buf = nullptr;
+  size_t pre_bytes = 0;
+  cudaStream_t pre_stream = nullptr;
+  cudaEvent_t pre_copied = nullptr, pre_consumed = nullptr;
+  bool pre_pending = false;    // a prefetched state waits to be loaded
+  bool pre_used = false;       // pre_consumed has been recorded at least once
+  int pre_dtype = 0, pre_layout = 0;
   bool has_state = false;
   int variant = -1;
   int grid = 0;
@@ -496,6 +504,13 @@ extern "C" void fv_destroy(fv_ctx *c) {
   if (c->snap_ready) cudaEventDestroy(c->snap_ready);
   if (c->snap_done) cudaEventDestroy(c->snap_done);
   if (c->snap_buf) cudaFree(c->snap_buf);
+  if (c->pre_stream) {
+    cudaStreamSynchronize(c->pre_stream);
+    cudaStreamDestroy(c->pre_stream);
+  }
+  if (c->pre_copied) cudaEventDestroy(c->pre_copied);
+  if (c->pre_consumed) cudaEventDestroy(c->pre_consumed);
+  if (c->pre_buf) cudaFree(c->pre_buf);
   free_graphs(c);
   for (int b = 0; b < 2; ++b)
     if (c->buf[b] && (b == 0 || c->buf[1] != c->buf[0])) cudaFree(c->buf[b]);
@@ -605,6 +620,51 @@ extern "C" fv_status fv_set_state(fv_ctx *c, const void *src, int src_is_device,
   FV_CUDA(c, launch_load_state(c->cfg.system, prec, dsrc, src_dtype == FV_F32, layout == FV_PRIMITIVE,
                                c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->cfg.params[0],
                                c->stream));
+  return seed(c, 0, 0.0, 0u);
+}
+
+extern "C" fv_status fv_prefetch_state(fv_ctx *c, const void *src, int src_dtype, int layout) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!src) return fail(c, FV_ERR_INVALID_ARG, "src is NULL");
+  if (src_dtype != FV_F64 && src_dtype != FV_F32) return fail(c, FV_ERR_INVALID_ARG, "bad src_dtype");
+  if (layout != FV_CONSERVED && layout != FV_PRIMITIVE) return fail(c, FV_ERR_INVALID_ARG, "bad layout");
+  if (!c->pre_stream) {
+    FV_CUDA(c, cudaStreamCreateWithFlags(&c->pre_stream, cudaStreamNonBlocking));
+    FV_CUDA(c, cudaEventCreateWithFlags(&c->pre_copied, cudaEventDisableTiming));
+    FV_CUDA(c, cudaEventCreateWithFlags(&c->pre_consumed, cudaEventDisableTiming));
+  }
+  const size_t need = (size_t)c->cfg.nx * c->cfg.ny * c->nvar * (src_dtype == FV_F64 ? 8 : 4);
+  if (c->pre_bytes < need) {
+    // the old buffer may still be read by a queued load or written by a copy
+    FV_CUDA(c, cudaStreamSynchronize(c->pre_stream));
+    FV_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->pre_buf) cudaFree(c->pre_buf);
+    c->pre_buf = nullptr;
+    c->pre_bytes = 0;
+    c->pre_used = false;
+    FV_CUDA(c, cudaMalloc(&c->pre_buf, need));
+    c->pre_bytes = need;
+  }
+  // the load of the previous prefetch must have read the buffer first
+  if (c->pre_used) FV_CUDA(c, cudaStreamWaitEvent(c->pre_stream, c->pre_consumed, 0));
+  FV_CUDA(c, cudaMemcpyAsync(c->pre_buf, src, need, cudaMemcpyHostToDevice, c->pre_stream));
+  FV_CUDA(c, cudaEventRecord(c->pre_copied, c->pre_stream));
+  c->pre_dtype = src_dtype;
+  c->pre_layout = layout;
+  c->pre_pending = true;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_set_state_prefetched(fv_ctx *c) {
+  if (!c) return FV_ERR_INVALID_ARG;
+  if (!c->pre_pending) return fail(c, FV_ERR_STATE, "no prefetched state");
+  c->pre_pending = false;
+  FV_CUDA(c, cudaStreamWaitEvent(c->stream, c->pre_copied, 0));
+  FV_CUDA(c, launch_load_state(c->cfg.system, c->cfg.precision, c->pre_buf, c->pre_dtype == FV_F32,
+                               c->pre_layout == FV_PRIMITIVE, c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
+                               c->plane, c->cfg.params[0], c->stream));
+  FV_CUDA(c, cudaEventRecord(c->pre_consumed, c->stream));
+  c->pre_used = true;
   return seed(c, 0, 0.0, 0u);
 }
 

@@ -7,8 +7,9 @@ and raises if the library is missing: there is no CPU fallback.
 
 Function names follow the ABI: fv_init, fv_set_state, fv_step, fv_run,
 fv_get_state, fv_totals, fv_time, fv_set_time, fv_lambda_max,
-fv_kernel_info, fv_gauss_legendre, fv_snapshot, fv_snapshot_wait, fv_destroy,
-plus the batched fv_batch_*.
+fv_kernel_info, fv_gauss_legendre, fv_snapshot, fv_snapshot_wait,
+fv_prefetch_state, fv_set_state_prefetched, fv_destroy, plus the batched
+fv_batch_*.
 """
 from __future__ import annotations
 
@@ -59,7 +60,8 @@ _lib = None
 EXPORTS = ("fv_status_string", "fv_last_error", "fv_init", "fv_destroy", "fv_set_state", "fv_step",
            "fv_run", "fv_get_state", "fv_totals", "fv_time", "fv_set_time", "fv_lambda_max",
            "fv_kernel_info", "fv_kernel_candidate", "fv_gauss_legendre", "fv_snapshot",
-           "fv_snapshot_wait", "fv_set_inplace", "fv_set_time_blocking", "fv_kernel_info_two_step")
+           "fv_snapshot_wait", "fv_set_inplace", "fv_set_time_blocking", "fv_kernel_info_two_step",
+           "fv_prefetch_state", "fv_set_state_prefetched")
 
 
 def library_path() -> str:
@@ -91,6 +93,8 @@ def load(build_if_missing: bool = True):
     L.fv_totals.argtypes = [vp, dp]
     L.fv_snapshot.argtypes = [vp, vp, ctypes.c_int]
     L.fv_snapshot_wait.argtypes = [vp]
+    L.fv_prefetch_state.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+    L.fv_set_state_prefetched.argtypes = [vp]
     L.fv_set_inplace.argtypes = [vp, ctypes.c_int]
     L.fv_set_time_blocking.argtypes = [vp, ctypes.c_int]
     L.fv_kernel_info_two_step.argtypes = [vp]
@@ -186,6 +190,11 @@ def _ptr(x):
     raise TypeError(f"unsupported buffer type {type(x)}")
 
 
+def _numel(x) -> int:
+    n = x.numel() if hasattr(x, "numel") else x.size
+    return int(n)
+
+
 def _dtype_code(x) -> int:
     s = str(x.dtype)
     if s.endswith("float64"):
@@ -224,7 +233,12 @@ class Solver:
     def __exit__(self, *a):
         self.close()
 
+    def _need(self, x):
+        if _numel(x) != self.nvar * self.ny * self.nx:
+            raise ValueError(f"expected {self.nvar} x {self.ny} x {self.nx} values, got {_numel(x)}")
+
     def set_state(self, src, primitive: bool = False, check: bool = True) -> int:
+        self._need(src)
         p, dev = _ptr(src)
         st = self.lib.fv_set_state(self.ctx, p, dev, _dtype_code(src), 1 if primitive else 0)
         if check:
@@ -246,6 +260,7 @@ class Solver:
         return dt.value
 
     def get_state(self, dst):
+        self._need(dst)
         p, dev = _ptr(dst)
         _check(self.lib.fv_get_state(self.ctx, p, dev, _dtype_code(dst)), self.ctx, self.lib)
         return dst
@@ -259,6 +274,7 @@ class Solver:
         """Queue an asynchronous copy of the current state into host memory
         `dst` (float32/float64, shape (nvar, ny, nx); pinned memory lets later
         steps overlap the copy).  Do not read dst before snapshot_wait()."""
+        self._need(dst)
         p, dev = _ptr(dst)
         if dev:
             raise ValueError("snapshot target must be host memory")
@@ -282,6 +298,26 @@ class Solver:
 
     def snapshot_wait(self):
         _check(self.lib.fv_snapshot_wait(self.ctx), self.ctx, self.lib)
+
+    def prefetch_state(self, src, primitive: bool = False):
+        """Queue an asynchronous copy of a state from host memory `src`
+        (float32/float64, shape (nvar, ny, nx); pinned memory lets the steps
+        already queued overlap the copy).  Keep src unchanged until
+        set_state_prefetched()."""
+        self._need(src)
+        p, dev = _ptr(src)
+        if dev:
+            raise ValueError("prefetch source must be host memory")
+        _check(self.lib.fv_prefetch_state(self.ctx, p, _dtype_code(src), 1 if primitive else 0),
+               self.ctx, self.lib)
+        return src
+
+    def set_state_prefetched(self, check: bool = True) -> int:
+        """set_state from the last prefetch_state (same results)."""
+        st = self.lib.fv_set_state_prefetched(self.ctx)
+        if check:
+            _check(st, self.ctx, self.lib)
+        return st
 
     def totals(self):
         import numpy as np
