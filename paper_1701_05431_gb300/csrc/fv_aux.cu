@@ -5,6 +5,8 @@
 // compensated conservation totals.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
@@ -36,6 +38,24 @@ __global__ void load_state_kernel(int system, const S *__restrict__ src, int pri
     const long long o = (long long)j * pitch + i;
     if (system == kAdvection) {
       state[o] = from_double<R>(rd(src, k));
+    } else if (std::is_same<S, float>::value && std::is_same<R, float>::value && system == kEuler) {
+      // FP32 in, FP32 state: a product of two FP32 values is exact in FP64,
+      // so rounding it to FP32 is the FP32 product; only rho E needs FP64
+      const float rho = (float)src[k], a1 = (float)src[ncell + k], a2 = (float)src[2 * ncell + k],
+                  a3 = (float)src[3 * ncell + k];
+      float w1 = a1, w2 = a2, w3 = a3;
+      if (primitive) {
+        const double u = a1, v = a2;
+        w1 = __fmul_rn(rho, a1);
+        w2 = __fmul_rn(rho, a2);
+        const double q = __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v));
+        w3 = (float)__dadd_rn(__ddiv_rn((double)a3, __dsub_rn(gamma, 1.0)),
+                              __dmul_rn(__dmul_rn((double)rho, q), 0.5));
+      }
+      state[o] = (R)rho;
+      state[plane + o] = (R)w1;
+      state[2 * plane + o] = (R)w2;
+      state[3 * plane + o] = (R)w3;
     } else if (system == kEuler) {
       double w0 = rd(src, k), w1 = rd(src, ncell + k), w2 = rd(src, 2 * ncell + k),
              w3 = rd(src, 3 * ncell + k);
@@ -224,7 +244,6 @@ static __device__ __forceinline__ void neu_merge(Neu &a, const Neu &b) {
 }
 
 constexpr int kTotThreads = 256;
-constexpr int kMaxVar = 8;
 
 int totals_blocks(int ny) { return ny < 1024 ? ny : 1024; }
 
