@@ -230,8 +230,11 @@ fv_status fv_set_time(fv_ctx *ctx, double t, long long step);
  * the two axis normals, the quantity bounded by Eq. (CFL_cond). */
 fv_status fv_lambda_max(fv_ctx *ctx, double *lmax);
 
-/* Kernel variant in use: *variant receives its index, *desc (nullable) a
- * static description such as "f32 v2 ty32 w4". */
+/* Kernel variant in use: *variant receives its index, *desc (nullable) its
+ * description such as "euler f32 v4 ty32 w4 b3 async4", followed by
+ * ", 35-row tasks" when the rows per warp task were balanced away from the
+ * kernel's nominal TY over the GPU's resident warps (the string stays valid
+ * until the next call on ctx). */
 fv_status fv_kernel_info(fv_ctx *ctx, int *variant, const char **desc);
 
 /* Description of the two-step kernel fv_run uses (fv_set_time_blocking),

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
@@ -90,6 +91,8 @@ struct fv_ctx {
   bool has_state = false;
   int variant = -1;
   int grid = 0;
+  int ty = 0;                    // rows per warp task of the selected kernel
+  std::string desc;              // its description with the task rows
   double dx = 0, dy = 0;
   std::map<int, cudaGraphExec_t> graphs;
   std::string err;
@@ -228,6 +231,33 @@ static void free_graphs(fv_ctx *c) {
   c->graphs.clear();
 }
 
+// Rows per warp task of an FP64 single-step kernel: within a quarter of its
+// TY, the count that minimises waves x (rows + 3), the time of a persistent
+// launch whose resident warps take the tasks round robin (a task costs its
+// rows plus about three: the halo row and the first row's fluxes); ties go
+// to the count nearest TY.  The model holds where the FP64 pipe bounds the
+// kernel, so that a task's time follows its rows (measured: 4.36 against
+// 4.08 G cell-updates/s on the 2048^2 four-quadrant case, 1.07 against 0.91
+// on 128^2 advection).  The FP32 and BF16 kernels are bound by HBM
+// bandwidth, which a last partial wave of warps still draws; balanced rows
+// made them slower (170 against 175 G on 8192^2), so they keep TY.
+static int balanced_rows(const fv_ctx *c, const Variant &V, int nb) {
+  const long long W = (long long)nb * V.NW * c->sms;
+  const long long nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
+  int best = V.TY;
+  long long best_cost = -1;
+  for (int ty = std::max(4, (3 * V.TY) / 4); ty <= (5 * V.TY) / 4; ++ty) {
+    const long long tasks = nstrips * ((c->cfg.ny + ty - 1) / ty);
+    const long long cost = ((tasks + W - 1) / W) * (ty + 3);
+    if (best_cost < 0 || cost < best_cost ||
+        (cost == best_cost && std::abs(ty - V.TY) < std::abs(best - V.TY))) {
+      best_cost = cost;
+      best = ty;
+    }
+  }
+  return best;
+}
+
 static fv_status select_variant(fv_ctx *c, int vi) {
   const Variant &V = all_variants()[vi];
   int nb = 0;
@@ -235,8 +265,9 @@ static fv_status select_variant(fv_ctx *c, int vi) {
     FV_CUDA(c, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
   FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));
   if (nb < 1) return fail(c, FV_ERR_CUDA, std::string("kernel cannot launch: ") + V.desc);
+  c->ty = (V.inplace || V.tb || V.precision != 0) ? V.TY : balanced_rows(c, V, nb);
   const int nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
-  const int nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
+  const int nchunks = (c->cfg.ny + c->ty - 1) / c->ty;
   const long long ntasks = (long long)nstrips * nchunks;
   long long need = (ntasks + V.NW - 1) / V.NW;
   long long grid = (long long)nb * c->sms;
@@ -265,7 +296,8 @@ static StepArgs<R> make_args(const fv_ctx *c, const Variant &V) {
   a.pitch = c->pitch;
   a.plane = c->plane;
   a.nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
-  a.nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
+  a.ty = (V.inplace || V.tb || c->ty < 1) ? V.TY : c->ty;
+  a.nchunks = (c->cfg.ny + a.ty - 1) / a.ty;
   a.ntasks = a.nstrips * a.nchunks;
   a.dx = c->dx;
   a.dy = c->dy;
@@ -956,7 +988,11 @@ extern "C" fv_status fv_kernel_info(fv_ctx *c, int *variant, const char **desc) 
       if (cand[k] == c->variant) idx = (int)k;
     *variant = idx;
   }
-  if (desc) *desc = V.desc;
+  if (desc) {
+    c->desc = V.desc;
+    if (!V.inplace && !V.tb && c->ty != V.TY) c->desc += ", " + std::to_string(c->ty) + "-row tasks";
+    *desc = c->desc.c_str();
+  }
   return FV_OK;
 }
 

@@ -42,6 +42,7 @@ template <class S> struct StepArgs {
   long long pitch;   // elements between rows
   long long plane;   // elements between variables
   int nstrips, nchunks, ntasks;
+  int ty;            // rows per warp task (the kernel's TY in place and two-step)
   double dx, dy;
   DtPolicy pol;
   SysParams<typename ParamOf<S>::T> sp;
@@ -1072,8 +1073,9 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
       const int sx_ = task % a.nstrips;
       const int cy = task / a.nstrips;
       const int X = sx_ * (30 * N) + (lane - 1) * N;
-      const int y0 = cy * TY;
-      const int y1 = min(y0 + TY, a.ny);
+      const int ty = INPL ? TY : a.ty;
+      const int y0 = cy * ty;
+      const int y1 = min(y0 + ty, a.ny);
       // warp-uniform: does every lane of the strip read real columns only?
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
       if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);

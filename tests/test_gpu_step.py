@@ -224,9 +224,10 @@ def test_default_kernel_fills_the_gpu_on_small_grids():
         big = wl.problem("euler", 8192, 8192)
         small = wl.problem("euler", 256, 256)
         with f.Solver(big, precision) as s:
-            assert s.kernel_info()[1] == first
+            # FP64 kernels may report rows per task balanced over the GPU
+            assert s.kernel_info()[1].split(",")[0] == first
         with f.Solver(small, precision) as s:
-            got = s.kernel_info()[1]
+            got = s.kernel_info()[1].split(",")[0]
         assert got != first and "ty16" in got, (precision, got)
 
 
