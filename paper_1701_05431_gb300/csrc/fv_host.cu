@@ -231,14 +231,14 @@ static void free_graphs(fv_ctx *c) {
   c->graphs.clear();
 }
 
-// Rows per warp task of an FP64 single-step kernel: within a quarter of its
-// TY, the count that minimises waves x (rows + 3), the time of a persistent
+// Rows per warp task of an FP64 single-step kernel: from TY/4 (at least 4)
+// to 5 TY/4, the count that minimises waves x (rows + 3), the time of a persistent
 // launch whose resident warps take the tasks round robin (a task costs its
 // rows plus about three: the halo row and the first row's fluxes); ties go
 // to the count nearest TY.  The model holds where the FP64 pipe bounds the
-// kernel, so that a task's time follows its rows (measured: 4.36 against
-// 4.08 G cell-updates/s on the 2048^2 four-quadrant case, 1.07 against 0.91
-// on 128^2 advection).  The FP32 and BF16 kernels are bound by HBM
+// kernel, so that a task's time follows its rows (measured: 4.35 against
+// 4.07 G cell-updates/s on the 2048^2 four-quadrant case, 1.66 against 0.91
+// on 128^2 advection, where one wave of 4-row tasks replaces 16-row ones).  The FP32 and BF16 kernels are bound by HBM
 // bandwidth, which a last partial wave of warps still draws; balanced rows
 // made them slower (170 against 175 G on 8192^2), so they keep TY.
 static int balanced_rows(const fv_ctx *c, const Variant &V, int nb) {
@@ -246,7 +246,7 @@ static int balanced_rows(const fv_ctx *c, const Variant &V, int nb) {
   const long long nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
   int best = V.TY;
   long long best_cost = -1;
-  for (int ty = std::max(4, (3 * V.TY) / 4); ty <= (5 * V.TY) / 4; ++ty) {
+  for (int ty = std::max(4, V.TY / 4); ty <= (5 * V.TY) / 4; ++ty) {
     const long long tasks = nstrips * ((c->cfg.ny + ty - 1) / ty);
     const long long cost = ((tasks + W - 1) / W) * (ty + 3);
     if (best_cost < 0 || cost < best_cost ||
