@@ -71,23 +71,39 @@ static __device__ __forceinline__ void me_moments(const double *nd, int Q, const
   }
 }
 
-// exp(-t) for |t| <= 2^-6: Taylor polynomial of degree 7 in Horner form
-// (truncation below e^|t| |t|^8 / 8! < 1e-19, a thousandth of an ulp).
+// Incremental updates of the cached exponentials: exp(-t) from its Taylor
+// polynomial of degree DEG (Horner form) for |t| <= Upd<R>::bound.  The pairs
+// keep the truncation e^|t| |t|^(DEG+1) / (DEG+1)! below 1e-19, a thousandth
+// of an ulp: degree 5 for |t| <= 2^-10, degree 7 for |t| <= 2^-6.  With FP64
+// storage the multipliers move smoothly between steps and the short update
+// serves nearly every evaluation (C5 FP64: 0.217 G cell-updates/s, against
+// 0.205 with degree 7 and 0.191 with degree 10 for 2^-6); with FP32 storage
+// the rounded moments move them by more, and the wider bound keeps more
+// evaluations incremental (0.194, against 0.163 with degree 5).
+template <class R> struct Upd {
+  static constexpr int deg = 7;
+  static constexpr double bound = 0x1p-6;
+};
+template <> struct Upd<double> {
+  static constexpr int deg = 5;
+  static constexpr double bound = 0x1p-10;
+};
+
+template <int DEG>
 static __device__ __forceinline__ double exp_neg_small(double t) {
+  constexpr double inv_fact[8] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0};
+  static_assert(DEG >= 1 && DEG <= 7, "degree 1..7");
   const double u = -t;
-  double p = 1.0 / 5040.0;
-  p = fma(p, u, 1.0 / 720.0);
-  p = fma(p, u, 1.0 / 120.0);
-  p = fma(p, u, 1.0 / 24.0);
-  p = fma(p, u, 1.0 / 6.0);
-  p = fma(p, u, 0.5);
-  p = fma(p, u, 1.0);
-  return fma(p, u, 1.0);
+  double p = inv_fact[DEG];
+#pragma unroll
+  for (int k = DEG - 1; k >= 0; --k) p = fma(p, u, inv_fact[k]);
+  return p;
 }
 
 // The moments after the multipliers moved by d, from the cached e_q of the
 // previous multipliers: e_q <- e_q exp(-(d0 + d1 x + d2 x^2 + d3 x^3)).
-// Requires |d0| + |d1| + |d2| + |d3| <= 2^-6.
+// Requires |d0| + |d1| + |d2| + |d3| <= the bound of degree DEG.
+template <int DEG>
 static __device__ __forceinline__ void me_moments_step(const double *nd, int Q, const double (&d)[4],
                                                        double (&M)[8], double *e, int es) {
 #pragma unroll
@@ -96,15 +112,13 @@ static __device__ __forceinline__ void me_moments_step(const double *nd, int Q, 
     const double *r = nd + q * kNodeStride;
     const double x = r[0];
     const double pd = fma(fma(fma(d[3], x, d[2]), x, d[1]), x, d[0]);
-    const double eq = e[q * es] * exp_neg_small(pd);
+    const double eq = e[q * es] * exp_neg_small<DEG>(pd);
     e[q * es] = eq;
 #pragma unroll
     for (int k = 0; k < 7; ++k) M[k] = fma(r[1 + k], eq, M[k]);
     M[7] = fma(r[8], eq, M[7]);
   }
 }
-
-constexpr double kIncrementalStep = 0x1p-6;
 
 // Cholesky solve of the 4 x 4 SPD system H d = r; false if H is not SPD.
 static __device__ __forceinline__ bool spd_solve4(const double (&M)[8], const double (&r)[4],
@@ -153,6 +167,7 @@ static __device__ __forceinline__ bool realizable(const double (&c)[4]) {
 
 // Maximum-entropy reconstruction: returns false when Newton fails.  e is
 // the thread's exponential cache (Q values, stride es).
+template <class U>
 static __device__ bool maxent(const double *nd, int Q, double tol, const double (&m)[4], double (&lam)[4],
                               double &n0, double &mmh, double *e, int es, int have0, const double (&d0)[4]) {
   double M[8];
@@ -164,7 +179,7 @@ static __device__ bool maxent(const double *nd, int Q, double tol, const double 
   double d[4] = {d0[0], d0[1], d0[2], d0[3]};
   for (int it = 0; it < 100; ++it) {
     if (have == 0) me_moments(nd, Q, lam, M, e, es);
-    else if (have == 1) me_moments_step(nd, Q, d, M, e, es);
+    else if (have == 1) me_moments_step<U::deg>(nd, Q, d, M, e, es);
     double r[4], worst = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -199,7 +214,7 @@ static __device__ bool maxent(const double *nd, int Q, double tol, const double 
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) lam[k] += d[k];
-      have = fabs(d[0]) + fabs(d[1]) + fabs(d[2]) + fabs(d[3]) <= kIncrementalStep ? 1 : 0;
+      have = fabs(d[0]) + fabs(d[1]) + fabs(d[2]) + fabs(d[3]) <= U::bound ? 1 : 0;
     }
   }
   if (!ok) {
@@ -280,14 +295,14 @@ fv_spray_source_kernel(const SourceArgs<R> a) {
           d0[q] = lam[q] - lam_prev[q];
           moved += fabs(d0[q]);
         }
-        if (moved <= kIncrementalStep) {
+        if (moved <= Upd<R>::bound) {
           for (int q = 0; q < a.Q; ++q) s_exp[q * kSrcThreads + threadIdx.x] = a.ecache[q * a.plane + o];
           have0 = 1;
         }
       }
       double n0 = 0.0, mmh = 0.0;
       if (!cell_bad)
-        cell_bad = !maxent(s_nodes, a.Q, a.tol, m, lam, n0, mmh, s_exp + threadIdx.x, kSrcThreads, have0, d0);
+        cell_bad = !maxent<Upd<R>>(s_nodes, a.Q, a.tol, m, lam, n0, mmh, s_exp + threadIdx.x, kSrcThreads, have0, d0);
       if (!cell_bad && a.ecache)
         for (int q = 0; q < a.Q; ++q) a.ecache[q * a.plane + o] = s_exp[q * kSrcThreads + threadIdx.x];
       if (!cell_bad) {
