@@ -226,6 +226,47 @@ cudaError_t launch_seed_lambda(int system, int prec, const void *state, int nx, 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ carried primitives
+// Planes 4..7 of an FP64 Euler state (u, v, p, c of every cell, Euler::prims
+// of planes 0..3), for the kernels that carry them from step to step.
+__global__ void fill_prims_kernel(double *__restrict__ state, int nx, int ny, long long pitch, long long plane,
+                                  SysParams<double> P) {
+  for (int j = blockIdx.y; j < ny; j += gridDim.y)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+    const long long o = (long long)j * pitch + i;
+    const double W[4] = {state[o], state[plane + o], state[2 * plane + o], state[3 * plane + o]};
+    double u, v, p, c;
+    Euler::prims(W, P, u, v, p, c);
+    state[4 * plane + o] = u;
+    state[5 * plane + o] = v;
+    state[6 * plane + o] = p;
+    state[7 * plane + o] = c;
+  }
+}
+
+// The same four values of the four boundary states (Dirichlet ghosts).
+__global__ void bc_prims_kernel(const double *__restrict__ bc, SysParams<double> P, double *__restrict__ out) {
+  const int s = threadIdx.x;
+  if (s >= 4) return;
+  const double W[4] = {bc[8 * s], bc[8 * s + 1], bc[8 * s + 2], bc[8 * s + 3]};
+  Euler::prims(W, P, out[4 * s], out[4 * s + 1], out[4 * s + 2], out[4 * s + 3]);
+}
+
+cudaError_t launch_fill_prims(double *state, int nx, int ny, long long pitch, long long plane, double gamma,
+                              cudaStream_t s) {
+  const int th = 256;
+  const dim3 g = grid_for(nx, ny, th);
+  SysParams<double> P{gamma, gamma - 1.0};
+  fill_prims_kernel<<<g, th, 0, s>>>(state, nx, ny, pitch, plane, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bc_prims(const double *bc_dev, double gamma, double *out_dev, cudaStream_t s) {
+  SysParams<double> P{gamma, gamma - 1.0};
+  bc_prims_kernel<<<1, 32, 0, s>>>(bc_dev, P, out_dev);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ totals
 // Neumaier compensated summation: s + c tracks the exact running sum far
 // better than s alone.

@@ -267,6 +267,7 @@ static __device__ __forceinline__ SysParams<A> splat_params(const SysParams<type
 // Scalar advection, F = a u: eigenvalue a.n.
 struct Advection {
   static constexpr int NV = 1;
+  static constexpr int NU = NV;  // variables the scheme updates (the rest are carried)
   template <class R>
   static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
                                                 R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {
@@ -290,6 +291,7 @@ struct Advection {
 // F.x = (rho u, rho u u + p, rho u v, u (rho E + p)), eigenvalues u -+ c, u.
 struct Euler {
   static constexpr int NV = 4;
+  static constexpr int NU = NV;
   template <class R>
   static __device__ __forceinline__ void prims(const R (&W)[NV], const SysParams<R> &P, R &u,
                                                R &v, R &p, R &c) {
@@ -331,10 +333,53 @@ struct Euler {
   }
 };
 
+// Euler with carried primitives (FP64 kernels): each cell stores, after its
+// four conserved variables, the u, v, p, c that Euler::prims gives for them
+// (planes 4..7).  The step that produces W^{n+1} computes those anyway for
+// the wave speed of Eq. (CFL_cond) and stores them; the next step's fluxes
+// read them instead of recomputing them, which saves one reciprocal, one
+// square root and ten operations per cell on the FP64 pipe.  The fluxes,
+// speeds and admissibility are those of Euler bit for bit.
+struct EulerPC {
+  static constexpr int NV = 8;  // planes loaded and stored
+  static constexpr int NU = 4;  // variables the scheme updates
+  template <class R>
+  static __device__ __forceinline__ void complete(R (&W)[NV], const SysParams<R> &P) {
+    R Wc[4] = {W[0], W[1], W[2], W[3]};
+    Euler::prims(Wc, P, W[4], W[5], W[6], W[7]);
+  }
+  template <class R>
+  static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
+                                                R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {
+    using O = Ops<R>;
+    const R u = W[4], v = W[5], p = W[6], c = W[7];
+    R Ep = O::add(W[3], p);
+    Fx[0] = W[1];
+    Fx[1] = O::fma(W[1], u, p);
+    Fx[2] = O::mul(W[1], v);
+    Fx[3] = O::mul(u, Ep);
+    Fy[0] = W[2];
+    Fy[1] = O::mul(W[2], u);
+    Fy[2] = O::fma(W[2], v, p);
+    Fy[3] = O::mul(v, Ep);
+    sx = O::add(O::abs(u), c);
+    sy = O::add(O::abs(v), c);
+  }
+  template <class R>
+  static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, unsigned &bad) {
+    using O = Ops<R>;
+    const R u = W[4], v = W[5], p = W[6], c = W[7];
+    R l = O::add(O::max(O::abs(u), O::abs(v)), c);
+    bad = O::not_pos(W[0]) | O::not_pos(p) | O::not_fin(l);
+    return l;
+  }
+};
+
 // Spray moments, Eq. (Essadki): W = (m0, m1/2, m1, m3/2, m1 u, m1 v), all
 // transported by u = (m1 u)/m1; every eigenvalue is u.n.
 struct Spray {
   static constexpr int NV = 6;
+  static constexpr int NU = NV;
   template <class R>
   static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
                                                 R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {

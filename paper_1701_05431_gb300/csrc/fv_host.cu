@@ -51,6 +51,11 @@ struct fv_ctx {
   size_t esize = 0;
   long long pitch = 0, plane = 0;
   size_t buf_bytes = 0;
+  // FP64 Euler: each state buffer also holds the primitives u, v, p, c of
+  // its cells (planes 4..7) for the kernels that carry them (Variant::carry)
+  int nplanes = 0;
+  bool pc_dirty = false;         // planes 4..7 of the current state are stale
+  double bc_pc[4][4] = {};       // primitives of the four boundary states
   // two time steps per launch (fixed dt, periodic): its kernel and grid
   int tb_variant = -1;
   int tb_grid = 0;
@@ -317,6 +322,9 @@ static StepArgs<R> make_args(const fv_ctx *c, const Variant &V) {
   for (int s = 0; s < 4; ++s) {
     a.bc[s] = c->cfg.bc[s];
     for (int v = 0; v < 8; ++v) a.bc_state[s][v] = (PT)c->cfg.bc_state[s][v];
+    // carried primitives of a Dirichlet ghost (slots 4..7)
+    if (V.carry)
+      for (int v = 0; v < 4; ++v) a.bc_state[s][4 + v] = (PT)c->bc_pc[s][v];
   }
   return a;
 }
@@ -451,7 +459,8 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
   // row and every V-wide vector access is aligned
   c->pitch = ((long long)cfg->nx + 31) / 32 * 32;
   c->plane = c->pitch * cfg->ny;
-  c->buf_bytes = (size_t)c->plane * c->nvar * c->esize;
+  c->nplanes = (cfg->system == FV_EULER && cfg->precision == FV_F64) ? 8 : c->nvar;
+  c->buf_bytes = (size_t)c->plane * c->nplanes * c->esize;
   c->dx = (cfg->xmax - cfg->xmin) / cfg->nx;
   c->dy = (cfg->ymax - cfg->ymin) / cfg->ny;
   c->stream = (cudaStream_t)cfg->stream;
@@ -501,6 +510,22 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     if ((e = cudaMalloc(&c->ecache, sizeof(double) * Q * c->plane)) != cudaSuccess)
       return bail(e, "cudaMalloc(exponential cache)");
     c->src_grid = spray_source_grid(cfg->precision == FV_F64 ? 0 : 1, Q, c->sms);
+  }
+  if (c->nplanes > c->nvar) {
+    // primitives of the boundary states, computed by the kernels' own prims
+    double *d_bc = nullptr;
+    double h_bc[32];
+    for (int s2 = 0; s2 < 4; ++s2)
+      for (int v = 0; v < 8; ++v) h_bc[8 * s2 + v] = cfg->bc_state[s2][v];
+    if ((e = cudaMalloc(&d_bc, sizeof(double) * 48)) != cudaSuccess) return bail(e, "cudaMalloc(bc)");
+    if ((e = cudaMemcpy(d_bc, h_bc, sizeof(h_bc), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = launch_bc_prims(d_bc, cfg->params[0], d_bc + 32, c->cap_stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->cap_stream)) != cudaSuccess ||
+        (e = cudaMemcpy(&c->bc_pc[0][0], d_bc + 32, sizeof(double) * 16, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      cudaFree(d_bc);
+      return bail(e, "boundary primitives");
+    }
+    cudaFree(d_bc);
   }
   int prec = cfg->precision;  // 0 f64, 1 f32, 2 bf16 storage
   int vi = default_variant_for(cfg->system, prec, cfg->nx, cfg->ny, c->sms);
@@ -602,6 +627,23 @@ static fv_status fill_ovl(fv_ctx *c, long long step) {
   return FV_OK;
 }
 
+// Planes 4..7 (carried primitives) of state buffer b from its planes 0..3.
+static fv_status fill_prims(fv_ctx *c, unsigned b) {
+  FV_CUDA(c, launch_fill_prims((double *)c->buf[b], c->cfg.nx, c->cfg.ny, c->pitch, c->plane, c->cfg.params[0],
+                               c->stream));
+  c->pc_dirty = false;
+  return FV_OK;
+}
+
+// Before a kernel that reads carried primitives: refresh them when a kernel
+// that does not carry them (in place, two steps per launch) wrote the state.
+static fv_status ensure_prims(fv_ctx *c) {
+  if (!c->pc_dirty || c->variant < 0 || !all_variants()[c->variant].carry) return FV_OK;
+  fv_status st = read_ctrl(c);
+  if (st != FV_OK) return st;
+  return fill_prims(c, c->h_ctrl->cur);
+}
+
 static fv_status seed(fv_ctx *c, long long step, double t, unsigned cur) {
   Ctrl h;
   std::memset(&h, 0, sizeof(h));
@@ -612,6 +654,10 @@ static fv_status seed(fv_ctx *c, long long step, double t, unsigned cur) {
   FV_CUDA(c, cudaMemcpyAsync(c->ctrl, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
   if (c->lamw)  // all-ones bytes are NaNs: every cell starts its Newton solve cold
     FV_CUDA(c, cudaMemsetAsync(c->lamw, 0xff, sizeof(double) * 12 * c->plane, c->stream));
+  if (c->nplanes > c->nvar) {
+    fv_status st0 = fill_prims(c, cur);
+    if (st0 != FV_OK) return st0;
+  }
   double p0 = c->cfg.params[0], p1 = c->cfg.params[1];
   if (c->cfg.system == FV_EULER) p1 = c->cfg.params[0] - 1.0;
   FV_CUDA(c, launch_seed_lambda(c->cfg.system, c->cfg.precision, c->buf[cur],
@@ -831,6 +877,10 @@ extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) 
   if (nsteps < 0) return fail(c, FV_ERR_INVALID_ARG, "nsteps < 0");
   if (!c->has_state) return fail(c, FV_ERR_STATE, "no state set");
   if (!std::isfinite(t_end)) return fail(c, FV_ERR_INVALID_ARG, "t_end must be finite");
+  {
+    fv_status st0 = ensure_prims(c);
+    if (st0 != FV_OK) return st0;
+  }
   // (a trial step would overwrite the state in place: no tuning there)
   if (c->cfg.tune == 1 && !c->tuned && nsteps > 0 && !c->inplace) {
     fv_status st = autotune(c);
@@ -857,6 +907,8 @@ extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) 
       FV_CUDA(c, cudaGraphLaunch(g, c->stream));
       passes -= n;
     }
+    // the two-step kernels update planes 0..3 only
+    if (c->nplanes > c->nvar) c->pc_dirty = true;
     st = read_ctrl(c);
     if (st != FV_OK) return st;
     if (c->h_ctrl->err_committed & kErrReplay) {
@@ -865,7 +917,12 @@ extern "C" fv_status fv_run(fv_ctx *c, int nsteps, double t_end, double *t_out) 
                                  cudaMemcpyHostToDevice, c->stream));
     }
     left = nsteps - (int)(c->h_ctrl->step - start);
+    if (left > 0) {
+      st = ensure_prims(c);
+      if (st != FV_OK) return st;
+    }
   }
+  if (left > 0 && c->nplanes > c->nvar && !all_variants()[c->variant].carry) c->pc_dirty = true;
   while (left > 0) {
     const int n = left >= chunk ? chunk : left;
     cudaGraphExec_t g;

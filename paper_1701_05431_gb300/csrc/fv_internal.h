@@ -25,6 +25,7 @@ struct Variant {
   const char *desc;
   int inplace;     // 1: in-place kernel (one state buffer plus overlap strips)
   int tb;          // 2: two time steps per launch (fixed dt, periodic); 0: one
+  int carry = 0;   // 1: FP64 Euler with carried primitives (planes 4..7 of the state)
 };
 
 // Registration hooks, one per translation unit of step kernels.
@@ -47,6 +48,12 @@ cudaError_t launch_totals(int prec, int nvar, const void *state, int nx, int ny,
                           long long plane, double *partials, int nblocks, double *out,
                           double cell_area, cudaStream_t s);
 int totals_blocks(int ny);
+// FP64 Euler with carried primitives: planes 4..7 (u, v, p, c) of a state
+// from its planes 0..3, and the same of the four boundary states (bc_dev:
+// 4 x 8 doubles, out_dev: 4 x 4 doubles).
+cudaError_t launch_fill_prims(double *state, int nx, int ny, long long pitch, long long plane, double gamma,
+                              cudaStream_t s);
+cudaError_t launch_bc_prims(const double *bc_dev, double gamma, double *out_dev, cudaStream_t s);
 
 // Record the message fv_last_error(NULL) returns (fv_host.cu).
 void set_global_error(const std::string &msg);

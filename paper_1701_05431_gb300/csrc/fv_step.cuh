@@ -260,14 +260,14 @@ static __device__ __forceinline__ void row_x(const SysParams<A> &P, const A (&W)
     const A sL = O::shift_in(sprev, sx[c]);
     const A sg = O::max(sL, sx[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    for (int v = 0; v < Sys::NU; ++v) {
       const A wprev = c == 0 ? O::shfl_up(W[V - 1][v], 1) : W[c - 1][v];
       const A fprev = c == 0 ? O::shfl_up(Fx[V - 1][v], 1) : Fx[c - 1][v];
       Fw[c][v] = lf_face2(O::shift_in(wprev, W[c][v]), O::shift_in(fprev, Fx[c][v]), W[c][v], Fx[c][v], sg);
     }
   }
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
+  for (int v = 0; v < Sys::NU; ++v) {
     const A first_next = O::shfl_down(Fw[0][v], 1);
 #pragma unroll
     for (int c = 0; c < V; ++c) {
@@ -459,11 +459,16 @@ static __device__ __forceinline__ void advance_row(const G &a, const SysParams<A
   for (int c = 0; c < V; ++c) {
     const A sg = O::max(cur.sy[c], nxt.sy[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    for (int v = 0; v < Sys::NU; ++v) {
       const A Fn = lf_face2(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], sg);
       Wn[c][v] = fv_update(cur.W[c][v], cur.dX[c][v], O::sub(Fn, Fs[c][v]), lx, ly);
       Fs[c][v] = Fn;
     }
+  }
+  // carried planes (primitives of the new state) follow from the updated ones
+  if constexpr (Sys::NU != Sys::NV) {
+#pragma unroll
+    for (int c = 0; c < V; ++c) Sys::complete(Wn[c], P);
   }
   // interior strip: XIN at compile time, or xin at run time
   const bool in = XIN || xin;
@@ -556,7 +561,7 @@ static __device__ __forceinline__ void march(const G &a, const SysParams<A> &P,
   for (int c = 0; c < V; ++c) {
     const A sg = O::max(RA.sy[c], RB.sy[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
+    for (int v = 0; v < Sys::NU; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
   }
   // the two row states swap roles every row (unrolled by two: no copies)
   int j = y0;
@@ -739,7 +744,7 @@ static __device__ __forceinline__ void march_tma(const G &a, const SysParams<A> 
   for (int c = 0; c < V; ++c) {
     const A sg = O::max(RA.sy[c], RB.sy[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
+    for (int v = 0; v < Sys::NU; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
   }
   int j = y0;
   while (true) {
@@ -979,7 +984,7 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
   for (int c = 0; c < V; ++c) {
     const A sg = O::max(RA.sy[c], RB.sy[c]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
+    for (int v = 0; v < Sys::NU; ++v) Fs[c][v] = lf_face2(RA.W[c][v], RA.Fy[c][v], RB.W[c][v], RB.Fy[c][v], sg);
   }
   int j = y0;
   while (true) {

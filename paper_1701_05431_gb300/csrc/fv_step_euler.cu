@@ -16,6 +16,14 @@ namespace fv {
                                 : (D) < 0 ? async_smem_bytes<A, V, 4, (D < 0 ? -D : 1)>(NW) : 0,         \
                         reinterpret_cast<const void *>(&fv_step_kernel<Euler, A, V, TY, NW, true, MB, D>), DESC})
 
+// FP64 two-buffer kernels: Euler with carried primitives (EulerPC, eight
+// planes per state: the conserved variables, then u, v, p, c).
+#define FV_VARIANT_PC(PREC, V, TY, NW, MB, D, DESC)                                                 \
+  out.push_back(Variant{kEuler, PREC, V, TY, NW, MB, D,                                               \
+                        (D) < 0 ? async_smem_bytes<double, V, 8, (D < 0 ? -D : 1)>(NW) : 0,            \
+                        reinterpret_cast<const void *>(&fv_step_kernel<EulerPC, double, V, TY, NW, true, MB, D>), \
+                        DESC, 0, 0, 1})
+
 // In-place kernels (cp.async ring only): one state buffer plus overlap strips.
 #define FV_VARIANT_INPL(A, PREC, V, TY, NW, MB, D, DESC)                                              \
   out.push_back(Variant{kEuler, PREC, (V) * Ops<A>::K, TY, NW, MB, D,                                   \
@@ -49,10 +57,10 @@ void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT_INPL(float, 1, 4, 64, 4, 3, -4, "euler f32 v4 ty64 w4 b3 async4 inplace");
   FV_VARIANT_INPL(BF, 2, 4, 32, 4, 3, -4, "euler bf16 v4 ty32 w4 b3 async4 inplace");
   FV_VARIANT_INPL(BF, 2, 2, 16, 4, 4, -6, "euler bf16 v2 ty16 w4 b4 async6 inplace");
-  FV_VARIANT(double, 0, 1, 64, 4, 1, 0, "euler f64 v1 ty64 w4");
-  FV_VARIANT(double, 0, 1, 32, 4, 1, 0, "euler f64 v1 ty32 w4");
-  FV_VARIANT(double, 0, 1, 16, 4, 1, 0, "euler f64 v1 ty16 w4");
-  FV_VARIANT(double, 0, 1, 64, 4, 4, -4, "euler f64 v1 ty64 w4 b4 async4");
+  FV_VARIANT_PC(0, 1, 64, 4, 1, 0, "euler f64 v1 ty64 w4 pc");
+  FV_VARIANT_PC(0, 1, 32, 4, 1, 0, "euler f64 v1 ty32 w4 pc");
+  FV_VARIANT_PC(0, 1, 16, 4, 1, 0, "euler f64 v1 ty16 w4 pc");
+  FV_VARIANT_PC(0, 1, 64, 4, 4, -4, "euler f64 v1 ty64 w4 b4 async4 pc");
   FV_VARIANT(float, 1, 4, 32, 4, 3, -4, "euler f32 v4 ty32 w4 b3 async4");
   FV_VARIANT(float, 1, 4, 64, 4, 3, -4, "euler f32 v4 ty64 w4 b3 async4");
   FV_VARIANT(float, 1, 4, 16, 4, 3, -4, "euler f32 v4 ty16 w4 b3 async4");
