@@ -107,7 +107,9 @@ const char *fv_status_string(fv_status s);
 const char *fv_last_error(const fv_ctx *ctx);
 
 /* Validate cfg and allocate every device buffer (two state buffers of
- * nVar x Ny x pitch values, a control block).  *out receives the context,
+ * nVar x Ny x pitch values -- 8 x Ny x pitch for FP64 Euler, whose kernels
+ * also keep the primitives u, v, p, c of every cell -- and a control
+ * block).  *out receives the context,
  * owned by the caller until fv_destroy.  FV_ERR_INVALID_ARG for a bad
  * configuration (unpaired periodic sides, non-positive sizes, unknown
  * system or precision), FV_ERR_OOM when allocation fails. */
