@@ -201,6 +201,26 @@ static int resident_blocks(const Variant &V) {
   return nb;
 }
 
+// Rows per warp task within [max(4, TY/4), 5 TY/4] that minimise waves x
+// (rows + 3) for an nx x ny grid over W resident warps (see balanced_rows);
+// *cost receives that product.
+static int balance_rows_for(const Variant &V, int nx, int ny, long long W, long long *cost) {
+  const long long nstrips = (nx + 30 * V.V - 1) / (30 * V.V);
+  int best = V.TY;
+  long long best_cost = -1;
+  for (int ty = std::max(4, V.TY / 4); ty <= (5 * V.TY) / 4; ++ty) {
+    const long long tasks = nstrips * ((ny + ty - 1) / ty);
+    const long long cst = ((tasks + W - 1) / W) * (ty + 3);
+    if (best_cost < 0 || cst < best_cost ||
+        (cst == best_cost && std::abs(ty - V.TY) < std::abs(best - V.TY))) {
+      best_cost = cst;
+      best = ty;
+    }
+  }
+  if (cost) *cost = best_cost;
+  return best;
+}
+
 // Default kernel for an nx x ny grid: the first candidate of (system,
 // precision), in the table's order of preference, whose warp tasks fill the
 // GPU (at least two per resident warp); if none does, the one with the most
@@ -209,6 +229,29 @@ static int default_variant_for(int system, int prec, int nx, int ny, int sms, in
   const auto &vs = all_variants();
   int best = -1;
   double best_ratio = -1.0;
+  if (prec == 0 && !inplace && !tb) {
+    // FP64 single-step kernels get their rows per task balanced: among the
+    // candidates of the first one's kind (same warps, register target and
+    // staging; TY and cells per lane differ), take the one whose balanced
+    // launch the time model finds shortest, a warp's row costing its cells
+    // per lane (the first of equals)
+    long long best_cost = -1;
+    const Variant *first = nullptr;
+    for (size_t k = 0; k < vs.size(); ++k) {
+      const Variant &V = vs[k];
+      if (V.system != system || V.precision != prec || V.inplace || V.tb) continue;
+      if (!first) first = &V;
+      if (V.NW != first->NW || V.MINB != first->MINB || V.D != first->D) continue;
+      long long cost = 0;
+      balance_rows_for(V, nx, ny, (long long)resident_blocks(V) * V.NW * sms, &cost);
+      cost *= V.V;
+      if (best_cost < 0 || cost < best_cost) {
+        best_cost = cost;
+        best = (int)k;
+      }
+    }
+    return best;
+  }
   for (size_t k = 0; k < vs.size(); ++k) {
     const Variant &V = vs[k];
     if (V.system != system || V.precision != prec || V.inplace != inplace || V.tb != tb) continue;
@@ -243,24 +286,12 @@ static void free_graphs(fv_ctx *c) {
 // to the count nearest TY.  The model holds where the FP64 pipe bounds the
 // kernel, so that a task's time follows its rows (measured: 4.35 against
 // 4.07 G cell-updates/s on the 2048^2 four-quadrant case, 1.66 against 0.91
-// on 128^2 advection, where one wave of 4-row tasks replaces 16-row ones).  The FP32 and BF16 kernels are bound by HBM
-// bandwidth, which a last partial wave of warps still draws; balanced rows
-// made them slower (170 against 175 G on 8192^2), so they keep TY.
+// on 128^2 advection, where one wave of 4-row tasks replaces 16-row ones).
+// The FP32 and BF16 kernels are bound by HBM bandwidth, which a last partial
+// wave of warps still draws; balanced rows made them slower (170 against 175
+// G on 8192^2), so they keep TY.
 static int balanced_rows(const fv_ctx *c, const Variant &V, int nb) {
-  const long long W = (long long)nb * V.NW * c->sms;
-  const long long nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
-  int best = V.TY;
-  long long best_cost = -1;
-  for (int ty = std::max(4, V.TY / 4); ty <= (5 * V.TY) / 4; ++ty) {
-    const long long tasks = nstrips * ((c->cfg.ny + ty - 1) / ty);
-    const long long cost = ((tasks + W - 1) / W) * (ty + 3);
-    if (best_cost < 0 || cost < best_cost ||
-        (cost == best_cost && std::abs(ty - V.TY) < std::abs(best - V.TY))) {
-      best_cost = cost;
-      best = ty;
-    }
-  }
-  return best;
+  return balance_rows_for(V, c->cfg.nx, c->cfg.ny, (long long)nb * V.NW * c->sms, nullptr);
 }
 
 static fv_status select_variant(fv_ctx *c, int vi) {
