@@ -637,21 +637,23 @@ static fv_status fill_ovl(fv_ctx *c, long long step) {
   const int sw = 30 * V.V;
   const int nstrips = (c->cfg.nx + sw - 1) / sw, nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
   void *dst = (char *)c->ovl + ((step & 1) ? c->ovl_parity_bytes : 0);
-  const long long total = (long long)nstrips * nchunks * c->nvar * (2 * V.TY + 2 * sw);
+  // kernels that carry the primitives keep them in the strips too
+  const int nv = V.carry ? c->nplanes : c->nvar;
+  const long long total = (long long)nstrips * nchunks * nv * (2 * V.TY + 2 * sw);
   const int th = 256;
   const int g = (int)std::min<long long>((total + th - 1) / th, 4LL * c->sms * 8);
   const int p = c->cfg.precision;
   if (p == 0)
     fill_ovl_kernel<double><<<g, th, 0, c->stream>>>((const double *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
-                                                     c->plane, c->nvar, nstrips, nchunks, V.TY, sw, c->ovl_task,
+                                                     c->plane, nv, nstrips, nchunks, V.TY, sw, c->ovl_task,
                                                      (double *)dst);
   else if (p == 1)
     fill_ovl_kernel<float><<<g, th, 0, c->stream>>>((const float *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
-                                                    c->plane, c->nvar, nstrips, nchunks, V.TY, sw, c->ovl_task,
+                                                    c->plane, nv, nstrips, nchunks, V.TY, sw, c->ovl_task,
                                                     (float *)dst);
   else
     fill_ovl_kernel<__nv_bfloat16><<<g, th, 0, c->stream>>>((const __nv_bfloat16 *)c->buf[0], c->cfg.nx, c->cfg.ny,
-                                                            c->pitch, c->plane, c->nvar, nstrips, nchunks, V.TY,
+                                                            c->pitch, c->plane, nv, nstrips, nchunks, V.TY,
                                                             sw, c->ovl_task, (__nv_bfloat16 *)dst);
   FV_CUDA(c, cudaGetLastError());
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1159,7 +1161,8 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
     const int sw = 30 * V.V;
     const long long ntasks = (long long)((c->cfg.nx + sw - 1) / sw) * ((c->cfg.ny + V.TY - 1) / V.TY);
     const int q = (int)(16 / c->esize);  // keep every task's strips 16-byte aligned
-    const int ts = (c->nvar * (2 * V.TY + 2 * sw) + q - 1) / q * q;
+    const int nv = V.carry ? c->nplanes : c->nvar;  // strips hold the carried planes too
+    const int ts = (nv * (2 * V.TY + 2 * sw) + q - 1) / q * q;
     const size_t pb = ((size_t)ntasks * ts * c->esize + 255) / 256 * 256;
     void *ovl = nullptr;
     cudaError_t e = cudaMalloc(&ovl, 2 * pb);
@@ -1179,7 +1182,11 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
     c->inplace = true;
     fv_status st = select_variant(c, vi);
     if (st != FV_OK) return st;
-    if (c->has_state) return fill_ovl(c, step);
+    if (c->has_state) {
+      st = ensure_prims(c);  // the strips copy the carried planes of the state
+      if (st != FV_OK) return st;
+      return fill_ovl(c, step);
+    }
     return FV_OK;
   }
   void *b1 = nullptr;

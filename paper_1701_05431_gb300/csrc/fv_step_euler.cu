@@ -24,6 +24,13 @@ namespace fv {
                         reinterpret_cast<const void *>(&fv_step_kernel<EulerPC, double, V, TY, NW, true, MB, D>), \
                         DESC, 0, 0, 1})
 
+// FP64 in-place kernels carry the primitives too (strips of eight variables).
+#define FV_VARIANT_INPL_PC(PREC, V, TY, NW, MB, D, DESC)                                            \
+  out.push_back(Variant{kEuler, PREC, V, TY, NW, MB, D,                                               \
+                        async_smem_bytes<double, V, 8, (D < 0 ? -D : 1)>(NW),                          \
+                        reinterpret_cast<const void *>(&fv_step_kernel<EulerPC, double, V, TY, NW, true, MB, D, true>), \
+                        DESC, 1, 0, 1})
+
 // In-place kernels (cp.async ring only): one state buffer plus overlap strips.
 #define FV_VARIANT_INPL(A, PREC, V, TY, NW, MB, D, DESC)                                              \
   out.push_back(Variant{kEuler, PREC, (V) * Ops<A>::K, TY, NW, MB, D,                                   \
@@ -49,8 +56,8 @@ void register_step_euler(std::vector<Variant> &out) {
   FV_VARIANT_TB(BF, 2, 2, 64, 4, 3, -4, "euler bf16 v2 ty64 w4 b3 async4 tb2");
   FV_VARIANT_TB(BF, 2, 2, 32, 4, 2, -4, "euler bf16 v2 ty32 w4 b2 async4 tb2");
   FV_VARIANT_TB(BF, 2, 2, 16, 4, 3, -4, "euler bf16 v2 ty16 w4 b3 async4 tb2");
-  FV_VARIANT_INPL(double, 0, 1, 64, 4, 3, -4, "euler f64 v1 ty64 w4 b3 async4 inplace");
-  FV_VARIANT_INPL(double, 0, 1, 16, 4, 3, -4, "euler f64 v1 ty16 w4 b3 async4 inplace");
+  FV_VARIANT_INPL_PC(0, 1, 64, 4, 3, -4, "euler f64 v1 ty64 w4 b3 async4 inplace pc");
+  FV_VARIANT_INPL_PC(0, 1, 16, 4, 3, -4, "euler f64 v1 ty16 w4 b3 async4 inplace pc");
   FV_VARIANT_INPL(float, 1, 4, 32, 4, 3, -4, "euler f32 v4 ty32 w4 b3 async4 inplace");
   FV_VARIANT_INPL(float, 1, 2, 16, 4, 4, -6, "euler f32 v2 ty16 w4 b4 async6 inplace");
   FV_VARIANT_INPL(float, 1, 2, 32, 4, 4, -6, "euler f32 v2 ty32 w4 b4 async6 inplace");
