@@ -16,10 +16,11 @@
 // evaluations instead of eight.
 // Only the first evaluation of a solve computes the Q exponentials
 // e_q = exp(-p(x_q)) (p the multipliers' polynomial); they stay in shared
-// memory, and after a Newton step d with sum |d_k| <= 2^-6 the next
-// evaluation multiplies them by exp(-p_d(x_q)), |p_d| <= 2^-6, from its
-// Taylor polynomial of degree 10 (truncation < 4e-28 relative), which costs
-// ten FMAs instead of an exponential per node.  The exponentials of each
+// memory, and after a Newton step d with sum |d_k| small (2^-10 with FP64
+// storage, 2^-6 with FP32) the next evaluation multiplies them by
+// exp(-p_d(x_q)), |p_d| within the same bound, from its Taylor polynomial of
+// degree 5 or 7 (truncation < 1e-19 relative), which costs five or seven
+// FMAs instead of an exponential per node.  The exponentials of each
 // cell's last solve are kept between steps too (Q planes), so that even the
 // first evaluation of a solve is such an update when the start is close to
 // the last solution; every 32 steps they are computed afresh.
