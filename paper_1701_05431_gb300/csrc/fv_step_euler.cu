@@ -3,7 +3,9 @@
 // two FP32 cells per packed FP32x2 instruction), values per lane V, rows per
 // warp task TY, warps per block NW, the blocks per SM the register budget
 // targets, and the row staging D (0 register prefetch, > 0 TMA ring,
-// < 0 cp.async ring).
+// < 0 cp.async ring).  The FP64 single-step and in-place kernels run the
+// EulerPC system: the same arithmetic, with each cell's primitives carried
+// in four more state planes from the step that computes them to the next.
 #include "fv_internal.h"
 #include "fv_step.cuh"
 #include "fv_tb.cuh"
