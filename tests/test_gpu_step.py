@@ -387,3 +387,36 @@ def test_t_end_clips_last_step():
     out, t, steps = gpu_run(d, prim, 1000, t_end=0.013)
     assert steps == ref.steps and abs(t - 0.013) <= 1e-15
     assert rel_linf(out, ref.W).max() <= 1e-12
+
+
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0, 1.1])
+def test_primitive_load_is_the_fp64_definition_bit_for_bit(gamma):
+    """rho E = p/(gamma - 1) + rho (u u + v v)/2 per cell, each operation
+    rounded once in FP64 (numpy's float64 arithmetic): the load divides by
+    gamma - 1 through a correction of the product with its reciprocal, which
+    must give the quotient itself."""
+    rng = np.random.default_rng(91)
+    ny, nx = 211, 173
+    prim = np.empty((4, ny, nx))
+    # wide magnitudes, kept admissible: p stays far above the rounding of
+    # rho E - rho (u u + v v)/2, so the load's check accepts every cell
+    prim[0] = rng.lognormal(0.0, 1.5, (ny, nx))
+    prim[1] = rng.normal(0.0, 1.0, (ny, nx))
+    prim[2] = rng.normal(0.0, 1.0, (ny, nx))
+    prim[3] = rng.lognormal(1.0, 1.0, (ny, nx)) + 0.1
+    d = wl.problem("euler", nx, ny, params=(gamma,))
+    rho, u, v, p = prim
+    q = u * u + v * v
+    want = np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + (rho * q) * 0.5])
+    with fv().Solver(d, "f64") as s:
+        s.set_state(np.ascontiguousarray(prim), primitive=True)
+        got = s.state()
+    assert np.array_equal(got, want)
+    # FP32 input and storage: the FP64 value rounded once to FP32
+    p32 = prim.astype(np.float32)
+    rho, u, v, p = (x.astype(np.float64) for x in p32)
+    want32 = np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + (rho * (u * u + v * v)) * 0.5]).astype(np.float32)
+    with fv().Solver(d, "f32") as s:
+        s.set_state(np.ascontiguousarray(p32), primitive=True)
+        got32 = s.state("float32")
+    assert np.array_equal(got32, want32)
