@@ -325,8 +325,8 @@ static const std::vector<BatchVariant> &batch_variants() {
     FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 5, -6, "batch euler f32 v1 ty64 w4 b5 async6");
     FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 6, -4, "batch euler f32 v1 ty64 w4 b6 async4");
     FV_BVARIANT(Euler, kEuler, float, 1, 1, 64, 4, 5, 0, "batch euler f32 v1 ty64 w4 b5");
-    FV_BVARIANT(Euler, kEuler, double, 0, 1, 32, 4, 3, 0, "batch euler f64 v1 ty32 w4 b3");
-    FV_BVARIANT(Euler, kEuler, double, 0, 1, 64, 4, 3, -4, "batch euler f64 v1 ty64 w4 b3 async4");
+    FV_BVARIANT(EulerPC, kEuler, double, 0, 1, 64, 4, 3, -4, "batch euler f64 v1 ty64 w4 b3 async4 pc");
+    FV_BVARIANT(EulerPC, kEuler, double, 0, 1, 32, 4, 2, 0, "batch euler f64 v1 ty32 w4 b2 pc");
     FV_BVARIANT(Advection, kAdvection, double, 0, 1, 32, 4, 4, 0, "batch advection f64 v1 ty32 w4 b4");
     FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, 0, "batch advection f32 v1 ty64 w4 b6");
     FV_BVARIANT(Advection, kAdvection, float, 1, 1, 64, 4, 6, -6, "batch advection f32 v1 ty64 w4 b6 async6");
@@ -341,6 +341,11 @@ using namespace fv;
 struct fv_batch {
   int n = 0;
   int system = 0, prec = 0, nvar = 0;
+  // FP64 Euler: each buffer also holds the primitives u, v, p, c of its cells
+  // (planes 4..7, the EulerPC system), and each instance's boundary states
+  // their primitives (4 sides x 4 values)
+  int nplanes = 0;
+  std::vector<double> bc_pc;
   size_t esize = 0;
   std::vector<fv_config> cfg;
   std::vector<long long> pitch, plane;
@@ -447,6 +452,8 @@ static void fill_args(const fv_batch *b, int k, const BatchVariant &V, StepArgs<
   for (int s = 0; s < 4; ++s) {
     a.bc[s] = c.bc[s];
     for (int v = 0; v < 8; ++v) a.bc_state[s][v] = (R)c.bc_state[s][v];
+    if (b->nplanes > b->nvar)  // carried primitives of a Dirichlet ghost
+      for (int v = 0; v < 4; ++v) a.bc_state[s][4 + v] = (R)b->bc_pc[16 * k + 4 * s + v];
   }
 }
 
@@ -537,6 +544,7 @@ extern "C" fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out)
       }
   }
   b->nvar = b->system == FV_ADVECTION ? 1 : 4;
+  b->nplanes = (b->system == FV_EULER && b->prec == 0) ? 8 : b->nvar;
   b->cfg.assign(cfgs, cfgs + n);
   b->stream = (cudaStream_t)cfgs[0].stream;
   b->has_state.assign(n, 0);
@@ -544,7 +552,7 @@ extern "C" fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out)
   for (int k = 0; k < n; ++k) {
     const long long pitch = ((long long)cfgs[k].nx + 31) / 32 * 32;
     const long long plane = pitch * cfgs[k].ny;
-    const size_t bytes = ((size_t)plane * b->nvar * b->esize + 255) / 256 * 256;
+    const size_t bytes = ((size_t)plane * b->nplanes * b->esize + 255) / 256 * 256;
     b->pitch.push_back(pitch);
     b->plane.push_back(plane);
     b->bytes.push_back(bytes);
@@ -583,6 +591,23 @@ extern "C" fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out)
   if ((e = cudaMemcpy(b->info, b->h_info, sizeof(RunInfo) * n, cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(e, "run info");
   if ((e = cudaMallocHost(&b->h_abort, sizeof(unsigned))) != cudaSuccess) return bail(e, "abort");
+  if (b->nplanes > b->nvar) {
+    // primitives of every instance's boundary states, by the kernels' own prims
+    b->bc_pc.assign((size_t)16 * n, 0.0);
+    double *d_bc = nullptr;
+    if ((e = cudaMalloc(&d_bc, sizeof(double) * 48)) != cudaSuccess) return bail(e, "bc");
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+      double h_bc[32];
+      for (int s2 = 0; s2 < 4; ++s2)
+        for (int v = 0; v < 8; ++v) h_bc[8 * s2 + v] = cfgs[k].bc_state[s2][v];
+      if ((e = cudaMemcpy(d_bc, h_bc, sizeof(h_bc), cudaMemcpyHostToDevice)) == cudaSuccess &&
+          (e = launch_bc_prims(d_bc, cfgs[k].params[0], d_bc + 32, b->cap_stream)) == cudaSuccess &&
+          (e = cudaStreamSynchronize(b->cap_stream)) == cudaSuccess)
+        e = cudaMemcpy(&b->bc_pc[16 * (size_t)k], d_bc + 32, sizeof(double) * 16, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(d_bc);
+    if (e != cudaSuccess) return bail(e, "boundary primitives");
+  }
   int vi = -1;
   const auto &vs = batch_variants();
   std::vector<int> cand;
@@ -647,6 +672,8 @@ extern "C" fv_status fv_batch_set_state(fv_batch *b, int k, const void *src, int
   void *buf0 = b->arena + b->off[k];
   FV_BCUDA(b, launch_load_state(b->system, b->prec, dsrc, src_dtype == FV_F32, layout == FV_PRIMITIVE, buf0,
                                 c.nx, c.ny, b->pitch[k], b->plane[k], c.params[0], b->stream));
+  if (b->nplanes > b->nvar)
+    FV_BCUDA(b, launch_fill_prims((double *)buf0, c.nx, c.ny, b->pitch[k], b->plane[k], c.params[0], b->stream));
   double p0 = c.params[0], p1 = c.params[1];
   if (b->system == FV_EULER) p1 = c.params[0] - 1.0;
   FV_BCUDA(b, launch_seed_lambda(b->system, b->prec, buf0, c.nx, c.ny, b->pitch[k], b->plane[k], p0, p1,

@@ -1,7 +1,8 @@
 """FP64 Euler kernels that carry the primitives (u, v, p, c) of every cell
-from step to step: their results are those of the kernels that recompute
-them (the batched kernel, the in-place and two-step kernels), bit for bit,
-on every boundary condition and across switches between the modes."""
+from step to step: their results are the batched kernel's (a separate code
+path, which carries them too) on every boundary condition, and those of the
+two-step kernel (which recomputes them) across switches between the modes,
+bit for bit."""
 from __future__ import annotations
 
 import numpy as np
@@ -43,7 +44,7 @@ def test_carried_primitives_match_the_batched_kernel(bc):
         s.set_state(prim, primitive=True)
         s.run(40)
         W, t = s.state(), s.time()
-    with f.Batch([d], "f64") as b:   # recomputes the primitives every step
+    with f.Batch([d], "f64") as b:
         b.set_state(0, prim, primitive=True)
         b.run(40)
         Wb, tb = b.state(0), b.time(0)
