@@ -289,7 +289,9 @@ typedef struct fv_batch fv_batch;
 
 /* Validate n >= 1 configurations (same system, precision, stream and tune;
  * spray is not batched) and allocate every instance's two state buffers in
- * one device arena.  tune >= 2 forces batched kernel candidate tune - 2. */
+ * one device arena (FP64 Euler: 8 planes per buffer, the conserved variables
+ * and the carried primitives u, v, p, c).  tune >= 2 forces batched kernel
+ * candidate tune - 2. */
 fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out);
 
 /* Load instance k's state at t = 0, step 0 (same conventions as
