@@ -30,7 +30,7 @@ from tests.helpers import oracle_problem  # noqa: E402
 CASES = {
     "c2": (lambda: wl.four_quadrant(2048, npart=8), 500),
     "c3": (lambda: wl.smooth_periodic(8192), 100),
-    "c5": (lambda: wl.spray_field(2048), 20),
+    "c5": (lambda: wl.spray_field(2048), 40),
 }
 
 

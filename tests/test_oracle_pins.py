@@ -407,6 +407,79 @@ def test_spray_evaporation_constant_density(oracle_mod):
     assert w[4] == 0.0 and w[5] == 0.0
 
 
+def test_spray_evaporation_momentum_keeps_velocity(oracle_mod):
+    """Momentum row of Eq. (Essadki) without drag: d(m1 u) = -K m0 u while
+    d m1 = -K m0, so a forward-Euler source step lowers m1 u by exactly
+    K m0 u dt and leaves u = (m1 u)/m1 unchanged, whatever the density.  For
+    n(S) = C the closed form is m1 u -> (C/2) u - K C u dt.  A momentum loss
+    proportional to m1 instead of m0, or of the wrong sign, changes u."""
+    C, K, dt = 0.8, 0.3, 0.01
+    u, v = 0.3, -0.2
+    m = [C / (1 + k / 2) for k in range(4)]
+    P = oracle_problem(wl.problem("spray", 4, 4, params=(K, 0.0, 0.0, 32.0, 1e-13)))
+    st, w = oracle.spray_source_cell(P, dt, 0.3, 0.6, m + [m[2] * u, m[2] * v])
+    assert st == oracle.OK
+    np.testing.assert_allclose(w[4], m[2] * u - K * C * u * dt, rtol=2e-15, atol=0)
+    np.testing.assert_allclose(w[5], m[2] * v - K * C * v * dt, rtol=2e-15, atol=0)
+    np.testing.assert_allclose([w[4] / w[2], w[5] / w[2]], [u, v], rtol=2e-15, atol=0)
+    # any realizable density: the velocity survives evaporation
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        mm = wl.canonical_to_moments(rng.uniform(0.5, 1.5), *rng.uniform(0.35, 0.75, 3))
+        uu, vv = rng.uniform(-1, 1, 2)
+        st, w = oracle.spray_source_cell(P, 1e-3, 0.1, 0.9, list(mm) + [mm[2] * uu, mm[2] * vv])
+        assert st == oracle.OK
+        np.testing.assert_allclose([w[4] / w[2], w[5] / w[2]], [uu, vv], rtol=1e-14, atol=1e-16)
+        np.testing.assert_allclose(w[4], mm[2] * uu - 1e-3 * K * mm[0] * uu, rtol=1e-14, atol=1e-17)
+    # through the time loop: a uniform field moving at (u, v) is not changed
+    # by transport, so one step is the source step alone in every cell
+    n = 6
+    prim = np.empty((6, n, n))
+    for k in range(4):
+        prim[k] = m[k]
+    prim[4], prim[5] = u, v
+    d = wl.problem("spray", n, n, fixed_dt=dt, params=(K, 0.0, 0.0, 32.0, 1e-13))
+    P, W0 = _state(d, prim)
+    r = oracle.run(P, W0, 1)
+    assert r.status == oracle.OK
+    np.testing.assert_allclose(r.W[4], m[2] * u - K * C * u * dt, rtol=2e-15, atol=0)
+    np.testing.assert_allclose(r.W[5] / r.W[2], v, rtol=2e-15, atol=0)
+
+
+def _taylor_green(nx, ny):
+    """Gas velocity of reading G15 at the cell centres of the unit square,
+    evaluated here independently of the oracle: u_g = sin 2pi x cos 2pi y,
+    v_g = -cos 2pi x sin 2pi y (rows are y, columns x)."""
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    ug = np.outer(np.cos(2 * np.pi * y), np.sin(2 * np.pi * x))
+    vg = -np.outer(np.sin(2 * np.pi * y), np.cos(2 * np.pi * x))
+    return ug, vg
+
+
+def test_spray_drag_toward_taylor_green_gas_field(oracle_mod):
+    """Drag of Eq. (Essadki) with the Taylor-Green gas field: droplets at
+    rest in a uniform field, no evaporation.  Transport moves nothing (u = 0),
+    so one step gives m1 u = dt m0 u_g(x_i, y_j) / theta cell by cell and keeps
+    every moment.  The grid is not square, so a swapped sin/cos, a sign or
+    x and y exchanged in the cell centres fail."""
+    nx, ny = 12, 8
+    theta, dt = 0.25, 0.003
+    m = wl.canonical_to_moments(1.1, 0.6, 0.3, 0.55)
+    prim = np.zeros((6, ny, nx))
+    for k in range(4):
+        prim[k] = m[k]
+    d = wl.problem("spray", nx, ny, fixed_dt=dt, params=(0.0, theta, 1.0, 32.0, 1e-13))
+    P, W0 = _state(d, prim)
+    r = oracle.run(P, W0, 1)
+    assert r.status == oracle.OK
+    ug, vg = _taylor_green(nx, ny)
+    np.testing.assert_allclose(r.W[4], dt * m[0] * ug / theta, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(r.W[5], dt * m[0] * vg / theta, rtol=0, atol=1e-16)
+    for k in range(4):
+        assert np.all(r.W[k] == m[k])
+
+
 def test_spray_drag_geometric_decay(oracle_mod):
     """Uniform field, no evaporation, gas at rest: u relaxes geometrically,
     u_N = u_0 (1 - dt m0 / (m1 theta))^N, with no spurious transport."""

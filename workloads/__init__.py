@@ -224,6 +224,34 @@ def spray_field(n: int = 2048, seed: int = SEED):
     return prim, problem("spray", n, n, cfl=0.4)
 
 
+def spray_field_wide(n: int = 2048, seed: int = SEED):
+    """Spray moments spread over the moment space: canonical moments
+    p_k = pbar_k + 0.2 sin(...) clipped to [0.05, 0.95], pbar_k ~ U[0.25, 0.75];
+    m0 = mbar (1 + 0.3 sin(...)), mbar ~ U[0.5, 1.5]; u, v = 0.5 sin(...).
+    The densities reach far from a constant (n(0) up to a few hundred), so
+    forward-Euler evaporation can leave the moment space after some steps.
+    Same problem description as spray_field."""
+    rng = np.random.default_rng(seed + 11)
+
+    def term():
+        return (int(rng.integers(1, 5)), int(rng.integers(1, 5)), float(rng.uniform(0, 2 * math.pi)))
+    pbar = [float(rng.uniform(0.25, 0.75)) for _ in range(3)]
+    mbar = float(rng.uniform(0.5, 1.5))
+    tp = [term() for _ in range(3)]
+    tm, tu, tv = term(), term(), term()
+    x = centres(n)
+    y = centres(n)
+    p = [np.clip(pbar[k] + _sin_sum(x, y, [tp[k]], 0.2), 0.05, 0.95) for k in range(3)]
+    m0 = mbar * (1.0 + _sin_sum(x, y, [tm], 0.3))
+    c = canonical_to_moments(m0, p[0], p[1], p[2])
+    prim = np.empty((6, n, n))
+    for k in range(4):
+        prim[k] = c[k]
+    prim[4] = _sin_sum(x, y, [tu], 0.5)
+    prim[5] = _sin_sum(x, y, [tv], 0.5)
+    return prim, problem("spray", n, n, cfl=0.4)
+
+
 # ---------------------------------------------------------------- validation cases
 def localized_cosine(n: int, repaired: bool = True, gamma: float = 1.4):
     """Sec. 5.1.1: density bump advected by (1, 1), p = 1/gamma.  The printed
