@@ -5,6 +5,9 @@ oracle needs minutes for these sizes, so it is not rerun here).
   C2: Euler 2048^2, four-quadrant Riemann data, 8 x 8 subdomains,
       transmissive, CFL 0.4, 500 steps, FP64.
   C3: Euler 8192^2, smooth periodic data, CFL 0.4, 100 steps, FP64 and FP32.
+  C5: spray moments 2048^2, periodic, CFL 0.4, 40 steps (the first full
+      recomputation of every cell's cached exponentials is at step 32),
+      FP64 and FP32 storage.
 
 FP64 <= 1e-12 relative L-infinity per variable over the samples; FP32
 <= 1e-5 relative L1 over the samples (smooth data).
@@ -80,6 +83,22 @@ def test_c3_smooth_8192(precision):
         l1 = np.abs(got - ref).sum(axis=1) / np.abs(ref).sum(axis=1)
         assert l1.max() <= 1e-5, l1
         assert abs(t - float(g["t"])) <= 1e-5 * float(g["t"])
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_c5_spray_2048(precision):
+    g = golden("c5")
+    prim, d = wl.spray_field(2048)
+    W, t, _ = run_full(d, prim, int(g["steps"]), precision)
+    got = sampled(W, g["flat_index"])
+    ref = g["W"]
+    if precision == "f64":
+        err = np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)
+        assert err.max() <= 1e-12, err
+        assert abs(t - float(g["t"])) <= 1e-13 * float(g["t"])
+    else:
+        l1 = np.abs(got - ref).sum(axis=1) / np.abs(ref).sum(axis=1)
+        assert l1.max() <= 1e-5, l1
 
 
 def test_c3_conservation_fp64_full():
