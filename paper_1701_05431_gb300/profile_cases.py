@@ -3,17 +3,14 @@
   python -m paper_1701_05431_gb300.profile_cases step --system euler --precision f32 --n 4096 --steps 3 [--inplace | --two-step]
   python -m paper_1701_05431_gb300.profile_cases batch --instances 96 --steps 4 --tune 2
   python -m paper_1701_05431_gb300.profile_cases spray --precision f64 --n 1024 --steps 3
-  python -m paper_1701_05431_gb300.profile_cases sweep --workload c3 --precision f32
+  python -m paper_1701_05431_gb300.profile_cases peak --seconds 0.02
 
 Each of the first three cases builds its seeded synthetic input (the
 `workloads` generators), copies it to the device, sets the state through the
 C ABI and advances the given number of time steps once; nothing is timed.
 `--tune K` (K >= 2) forces kernel candidate K - 2, so that a capture sees a
-known kernel.  `sweep` times every compiled candidate in turn on one workload
-(c3: Euler 8192^2 smooth periodic; c2: four-quadrant 2048^2; c4: 512 batched
-instances; c3tb: the c3 grid in fixed-dt mode with two-step passes;
-c3inplace: the c3 grid with one state buffer) with CUDA events and prints one
-JSON line per candidate.
+known kernel.  `peak` runs the FMA-pipe throughput measurement
+(fv_fma_peak) in FP64 and FP32 once each.
 """
 from __future__ import annotations
 
@@ -75,102 +72,17 @@ def batch_case(instances: int, steps: int, tune: int, precision: str = "f32") ->
         return b.kernel_info()[1]
 
 
-def _timed(fn, reps=3):
-    """Median device time (s) of fn() after one untimed call."""
-    import torch
-    stream = torch.cuda.current_stream()
-    fn()
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1) / 1e3)
-    return sorted(ts)[len(ts) // 2]
-
-
-def sweep(workload: str, precision: str, steps: int) -> None:
-    import json
-    import numpy as np
-    import torch
-    import workloads as wl
+def peak_case(seconds: float) -> str:
     from paper_1701_05431_gb300 import fvlib
-    stream = torch.cuda.current_stream().cuda_stream
-    if workload == "c4":
-        insts = wl.batched_quadrants(512)
-        ncells = sum(d["nx"] * d["ny"] for _, _, d in insts)
-        k = 0
-        while True:
-            try:
-                b = fvlib.Batch([d for _, _, d in insts], precision, stream=stream, tune=2 + k)
-            except fvlib.FvError:
-                break
-            with b:
-                for i, (_, prim, _) in enumerate(insts):
-                    b.set_state(i, prim, primitive=True)
-                sec = _timed(lambda: b.run(steps), 2)
-                print(json.dumps({"workload": workload, "precision": precision, "kernel": b.kernel_info()[1],
-                                  "cell_updates_per_s": ncells * steps / sec}), flush=True)
-            k += 1
-        return
-    if workload == "c3inplace":
-        # one state buffer, every in-place candidate
-        prim, d = wl.smooth_periodic(8192, dtype=np.float32)
-        dev = _device(prim)
-        k = 0
-        while True:
-            with fvlib.Solver(d, precision, stream=stream, tune=2 + k) as s:
-                try:
-                    s.set_inplace(True)
-                except fvlib.FvError:
-                    break
-                s.set_state(dev, primitive=True)
-                sec = _timed(lambda: s.run(steps))
-                print(json.dumps({"workload": workload, "precision": precision, "kernel": s.kernel_info()[1],
-                                  "cell_updates_per_s": d["nx"] * d["ny"] * steps / sec}), flush=True)
-            k += 1
-        return
-    if workload == "c3tb":
-        # two-step passes, fixed dt = 0.4 min(dx, dy) / lmax(W^0), every two-step candidate
-        prim, d = wl.smooth_periodic(8192, dtype=np.float32)
-        rho, u, v, p = (np.asarray(q, dtype=np.float64) for q in prim)
-        lam0 = float(np.max(np.maximum(np.abs(u), np.abs(v)) + np.sqrt(1.4 * p / rho)))
-        d = dict(d, fixed_dt=0.4 / 8192 / lam0)
-        dev = _device(prim)
-        k = 0
-        while True:
-            with fvlib.Solver(d, precision, stream=stream, tune=2 + k) as s:
-                try:
-                    s.set_time_blocking(2)
-                except fvlib.FvError:
-                    break
-                s.set_state(dev, primitive=True)
-                sec = _timed(lambda: s.run(steps))
-                print(json.dumps({"workload": workload, "precision": precision, "candidate": k,
-                                  "cell_updates_per_s": d["nx"] * d["ny"] * steps / sec}), flush=True)
-            k += 1
-        return
-    if workload == "c3":
-        prim, d = wl.smooth_periodic(8192, dtype=np.float32)
-    else:
-        prim, d = wl.four_quadrant(2048, npart=8)
-    dev = _device(prim)
-    for k in range(len(fvlib.kernel_candidates("euler", precision))):
-        with fvlib.Solver(d, precision, stream=stream, tune=2 + k) as s:
-            s.set_state(dev, primitive=True)
-            sec = _timed(lambda: s.run(steps))
-            print(json.dumps({"workload": workload, "precision": precision, "kernel": s.kernel_info()[1],
-                              "cell_updates_per_s": d["nx"] * d["ny"] * steps / sec}), flush=True)
+    r64 = fvlib.fma_peak("f64", seconds)
+    r32 = fvlib.fma_peak("f32", seconds)
+    return f"DFMA {r64:.4g}/s, FFMA {r32:.4g}/s"
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["step", "batch", "spray", "sweep"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c3tb", "c3inplace"])
+    ap.add_argument("case", choices=["step", "batch", "spray", "peak"])
+    ap.add_argument("--seconds", type=float, default=0.02, help="peak case: length of each timed launch")
     ap.add_argument("--system", default="euler", choices=["euler", "advection"])
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--n", type=int, default=4096)
@@ -181,10 +93,9 @@ def main(argv=None):
     ap.add_argument("--two-step", action="store_true",
                     help="step case (Euler): fixed dt and two time steps per launch (fv_set_time_blocking)")
     a = ap.parse_args(argv)
-    if a.case == "sweep":
-        sweep(a.workload, a.precision, a.steps)
-        return
-    if a.case == "step":
+    if a.case == "peak":
+        k = peak_case(a.seconds)
+    elif a.case == "step":
         k = step_case(a.system, a.precision, a.n, a.steps, a.tune, a.inplace, a.two_step)
     elif a.case == "spray":
         k = step_case("spray", a.precision, a.n, a.steps, a.tune)
