@@ -34,6 +34,7 @@ import workloads as wl  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0   # NVIDIA's HBM3e figure for GB300, for context beside the measured copy rate
 
 
 def peaks():
@@ -61,6 +62,9 @@ WORKLOADS = {
 METRIC = "cell-updates/s (FP32-bulk; FP64 plain beside it) and HBM GB/s"
 
 BYTES_PER_CELL = {"advection": 1, "euler": 4, "spray": 6}  # nvar
+# names of the per-configuration entries of accuracy_vs_oracle
+WORKLOAD_KEYS = {"c3": "c3_euler_8192", "c2": "c2_four_quadrant_2048", "c1": "c1_advection_128",
+                 "c3s": "c3_euler_4096"}
 
 
 class Clocks:
@@ -134,6 +138,50 @@ def measured_traffic_per_cell(kernel_desc: str):
     except OSError:
         pass
     return None
+
+
+FP64_OPS_FILE = os.path.join(ROOT, "profiles", "fp64_ops.txt")
+
+
+def measured_fp64_ops_per_cell(kernel_desc: str):
+    """FP64 work per cell-update of a kernel from the ncu capture recorded next
+    to the profile summaries: {"dfma", "dmul", "dadd", "pipe"} thread-level
+    instructions per cell-update (pipe: every instruction the FP64 pipe
+    executed), or None when that kernel was not captured."""
+    try:
+        with open(FP64_OPS_FILE) as f:
+            for line in f:
+                if line.startswith("#") or "|" not in line:
+                    continue
+                parts = [x.strip() for x in line.split("|")]
+                if parts[0] == kernel_desc and len(parts) >= 5:
+                    return dict(zip(("dfma", "dmul", "dadd", "pipe"), map(float, parts[1:5])))
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def fp64_roofline(kernel_desc: str, cell_updates_per_s: float, dfma_peak: float):
+    """Arithmetic roofline of an FP64-pipe-bound kernel: FP64 FLOP/s retired
+    (2 per DFMA, 1 per DMUL or DADD, counted per cell-update by ncu) against
+    twice the measured DFMA rate, and the FP64 pipe's instruction rate against
+    the measured DFMA rate (every FP64-pipe instruction takes the pipe as long
+    as a DFMA)."""
+    # the rows per warp task (", N-row tasks") change the halo share by a few
+    # per cent only; the capture is keyed by the kernel itself
+    ops = measured_fp64_ops_per_cell(kernel_desc.split(", ")[0])
+    out = {"bound": "alu", "unit": "TFLOP/s", "peak": 2 * dfma_peak / 1e12,
+           "peak_source": "measured: fv_fma_peak (DFMA chains on every SM, CUDA events) x 2 FLOP",
+           "peak_nominal": 1.25, "ops_per_cell_update": ops}
+    if ops is None or not dfma_peak:
+        out.update(achieved=None, frac=None, pipe_frac=None)
+        return out
+    flops = (2 * ops["dfma"] + ops["dmul"] + ops["dadd"]) * cell_updates_per_s
+    out.update(achieved=flops / 1e12, frac=flops / (2 * dfma_peak), frac_nominal=flops / 1.25e12,
+               pipe_frac=ops["pipe"] * cell_updates_per_s / dfma_peak,
+               ops_source="ncu sm__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on.sum and "
+                          "sm__thread_inst_executed_pipe_fp64_pred_on.sum of one launch (profiles/fp64_ops.txt)")
+    return out
 
 
 def max_over_ranks(value: float, device: str = "cpu") -> float:
@@ -264,7 +312,52 @@ def run_reference(args):
     return 0
 
 
-def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
+def errors_vs(got, ref):
+    """Per-variable relative L1 (sum|a-b| / sum|b|) and relative L-infinity
+    (max|a-b| / max|b|) of `got` against the oracle's `ref` (nvar x cells)."""
+    got = np.asarray(got, dtype=np.float64).reshape(ref.shape[0], -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(ref.shape[0], -1)
+    l1 = (np.abs(got - ref).sum(axis=1) / np.abs(ref).sum(axis=1)).tolist()
+    linf = (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).tolist()
+    return {"rel_l1": l1, "rel_linf": linf}
+
+
+def c4_accuracy(fvlib, b, insts, pick, sptr):
+    """FP32 batched states of the picked instances after 200 steps against the
+    FP64 oracle run of each instance (and the FP64 batched kernel on the same
+    instances)."""
+    import oracle
+    from tests.helpers import oracle_problem
+    oracle.build()
+    res = {"instances": [], "steps": 200,
+           "against": "oracle.run of each instance, 200 FP64 steps, every cell"}
+    refs = []
+    for k in pick:
+        _, pr, dd = insts[k]
+        P = oracle_problem(dd)
+        r = oracle.run(P, oracle.prim_to_cons(P, pr), 200)
+        refs.append(r.W)
+        e = errors_vs(b.state(k), r.W)
+        res["instances"].append({"index": k, "nx": dd["nx"], "ny": dd["ny"], "oracle_status": int(r.status),
+                                 "f32": e})
+    with fvlib.Batch([insts[k][2] for k in pick], "f64", stream=sptr) as b64:
+        for q, k in enumerate(pick):
+            b64.set_state(q, insts[k][1], primitive=True)
+        b64.run(200)
+        for q in range(len(pick)):
+            res["instances"][q]["f64"] = errors_vs(b64.state(q), refs[q])
+    for prec in ("f32", "f64"):
+        res[prec] = {"rel_l1": np.max([x[prec]["rel_l1"] for x in res["instances"]], axis=0).tolist(),
+                     "rel_linf": np.max([x[prec]["rel_linf"] for x in res["instances"]], axis=0).tolist()}
+    return res
+
+
+def golden_samples(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle_samples.npz")
+    return np.load(path) if os.path.exists(path) else None
+
+
+def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False, accuracy=None, dfma_peak=None):
     """The other configurations of the hot path, one or two timed jobs each
     (device-resident inputs, CUDA events around the run calls)."""
     out = {}
@@ -288,23 +381,42 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
         s.set_state(torch.from_numpy(prim).to(f"cuda:{local}"), primitive=True)
         sec = timed(lambda: s.run(100), 5)
         out["c1_advection_128_f64"] = {"cell_updates_per_s": 128 * 128 * 100 / sec, "ms_per_job": sec * 1e3,
-                                       "kernel": s.kernel_info()[1]}
+                                       "kernel": s.kernel_info()[1], "kernel_choice": s.kernel_choice()}
+        if accuracy is not None:
+            import oracle
+            from tests.helpers import oracle_problem
+            oracle.build()
+            P = oracle_problem(d)
+            ref = oracle.run(P, oracle.prim_to_cons(P, prim), 100)
+            s.set_state(torch.from_numpy(prim).to(f"cuda:{local}"), primitive=True)
+            s.run(100)
+            accuracy["c1_advection_128"] = {"f64": errors_vs(s.state(), ref.W), "samples": 128 * 128,
+                                            "steps": 100, "against": "oracle.run of the whole job, every cell"}
     if oracle_too:
         out["c1_advection_128_f64"]["oracle"] = oracle_sample(d, prim, 100, "the whole job")
     # C2: four-quadrant Euler 2048^2, 8x8 subdomains, FP64, 500 steps (and FP32)
     prim, d = wl.four_quadrant(2048, npart=8)
     pd = torch.from_numpy(prim).to(f"cuda:{local}")
+    g2 = golden_samples("c2")
+    acc2 = {}
     for precision in ("f64", "f32"):
         with fvlib.Solver(d, precision, stream=sptr) as s:
             def job():
                 s.set_state(pd, primitive=True)
                 s.run(500)
             sec = timed(job, 1)
+            if g2 is not None and accuracy is not None:
+                # the state after the last timed job is the 500-step result
+                acc2[precision] = errors_vs(s.state().reshape(4, -1)[:, g2["flat_index"]], g2["W"])
             nb = 2 * 4 * (8 if precision == "f64" else 4) * 2048 * 2048 * 500
             out[f"c2_four_quadrant_2048_{precision}"] = {
                 "cell_updates_per_s": 2048 * 2048 * 500 / sec, "ms_per_job": sec * 1e3,
                 "hbm_gbs_algorithmic": nb / sec / 1e9, "kernel": s.kernel_info()[1],
+                "kernel_choice": s.kernel_choice(),
                 "note": "job = set_state from device + 500 steps; 134 MB/268 MB state, close to L2 size"}
+    if acc2:
+        accuracy["c2_four_quadrant_2048"] = dict(acc2, samples=int(len(g2["flat_index"])), steps=500,
+                                                 against="stored oracle samples (tests/golden/c2_oracle_samples.npz)")
     if oracle_too:
         out["c2_four_quadrant_2048_f64"]["oracle"] = oracle_sample(d, prim, 5, "a sample")
     del pd
@@ -321,16 +433,27 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
             secs += dd["nx"] * dd["ny"] * 20 / o["value"]
         c4_oracle = {"value": cells / secs, "unit": "cell-updates/s", "cores": o["cores"],
                      "sample": f"the first 8 of the 512 instances, 20 FP64 steps each, {secs:.2f} s"}
-    with fvlib.Batch([dd for _, _, dd in insts], "f32", stream=sptr, tune=1) as b:
+    with fvlib.Batch([dd for _, _, dd in insts], "f32", stream=sptr) as b:
         for k, (_, pr, _) in enumerate(insts):
             b.set_state(k, pr, primitive=True)
-        del insts
         sec = timed(lambda: b.run(200), 2)
+        if accuracy is not None:
+            # outside the timed region: every instance restarted and advanced
+            # 200 steps by the same batched launch, then the three smallest
+            # instances and the largest compared with the oracle
+            for k, (_, pr, _) in enumerate(insts):
+                b.set_state(k, pr, primitive=True)
+            b.run(200)
+            sizes = [dd["nx"] * dd["ny"] for _, _, dd in insts]
+            order = sorted(range(len(insts)), key=lambda k: sizes[k])
+            pick = order[:3] + order[-1:]
+            accuracy["c4_batched_512"] = c4_accuracy(fvlib, b, insts, pick, sptr)
+        del insts
         nb = 2 * 4 * 4 * ncells * 200
         out["c4_batched_512_f32"] = {"cell_updates_per_s": ncells * 200 / sec, "ms_per_job": sec * 1e3,
                                      "cells": ncells, "hbm_gbs_algorithmic": nb / sec / 1e9,
                                      "hbm_frac": nb / sec / 1e9 / hbm, "kernel": b.kernel_info()[1],
-                                     "kernel_choice": "autotuned (one timed step per candidate before the first run)",
+                                     "kernel_choice": b.kernel_choice(),
                                      "launches_per_job": 1}
         if c4_oracle:
             out["c4_batched_512_f32"]["oracle"] = c4_oracle
@@ -348,14 +471,15 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
     insts = wl.batched_quadrants(512)
     cfgs = [fixed(pr, dd) for _, pr, dd in insts]
     for mode in ("gated", "dataflow"):
-        with fvlib.Batch(cfgs, "f32", stream=sptr, tune=1) as b:
+        with fvlib.Batch(cfgs, "f32", stream=sptr) as b:
             for k, (_, pr, _) in enumerate(insts):
                 b.set_state(k, pr, primitive=True)
             b.set_dataflow(mode == "dataflow")
             sec = timed(lambda: b.run(200), 1)
             out[f"c4_fixed_dt_{mode}_f32"] = {
                 "cell_updates_per_s": ncells * 200 / sec, "ms_per_job": sec * 1e3,
-                "hbm_frac": 2 * 4 * 4 * ncells * 200 / sec / 1e9 / hbm, "kernel": b.kernel_info()[1]}
+                "hbm_frac": 2 * 4 * 4 * ncells * 200 / sec / 1e9 / hbm, "kernel": b.kernel_info()[1],
+                "kernel_choice": b.kernel_choice()}
     del insts, cfgs
     prim, d = wl.smooth_periodic(8192, dtype=np.float32)
     dfix = fixed(prim, d)
@@ -379,9 +503,11 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
             out[f"c3_fixed_dt_two_steps_per_launch_{precision}"] = {
                 "cell_updates_per_s": 8192 * 8192 * 100 / sec, "ms_per_job": sec * 1e3,
                 "algorithmic_bytes_per_cell_update": (16 if precision == "f32" else 8),
-                "kernel": s.two_step_kernel(),
+                "kernel": s.two_step_kernel(), "kernel_choice": s.kernel_choice(two_step=True),
                 "note": "job = set_state from device + 100 steps = 50 launches"}
     for mode in ("gated", "dataflow"):
+        # one large instance: the batched table entry is keyed by total cells
+        # and measured on 512 small instances, so these time their candidates
         with fvlib.Batch([dfix], "f32", stream=sptr, tune=1) as b:
             b.set_dataflow(mode == "dataflow")
 
@@ -391,7 +517,8 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
             sec = timed(job, 1)
             out[f"c3_fixed_dt_batch_of_one_{mode}_f32"] = {
                 "cell_updates_per_s": 8192 * 8192 * 100 / sec, "ms_per_job": sec * 1e3,
-                "kernel": b.kernel_info()[1], "note": "job = set_state from device + 100 steps, one launch"}
+                "kernel": b.kernel_info()[1], "kernel_choice": b.kernel_choice(),
+                "note": "job = set_state from device + 100 steps, one launch"}
     del pd
     # f2: the headline job with one state buffer updated in place (halos from
     # overlap strips) instead of two
@@ -408,12 +535,14 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
             nsteps = 100 if precision == "f32" else 10
             out[f"c3_inplace_{precision}"] = {
                 "cell_updates_per_s": 8192 * 8192 * nsteps / sec, "ms_per_job": sec * 1e3,
-                "kernel": s.kernel_info()[1],
+                "kernel": s.kernel_info()[1], "kernel_choice": s.kernel_choice(),
                 "note": f"job = set_state from device + {nsteps} steps; one state buffer + overlap strips"}
     del pd
     # C5: spray moments 2048^2, periodic, 200 steps; FP64 plain and FP32-bulk
     prim, d = wl.spray_field(2048)
     pd = torch.from_numpy(prim).to(f"cuda:{local}")
+    g5 = golden_samples("c5")
+    acc5 = {}
     for precision in ("f64", "f32"):
         with fvlib.Solver(d, precision, stream=sptr) as s:
             s.set_state(pd, primitive=True)
@@ -428,8 +557,18 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False):
             sec = e0.elapsed_time(e1) / 1e3
             out[f"c5_spray_2048_{precision}"] = {
                 "cell_updates_per_s": 2048 * 2048 * 200 / sec, "ms_per_job": sec * 1e3,
-                "kernel": s.kernel_info()[1],
+                "kernel": s.kernel_info()[1], "kernel_choice": s.kernel_choice(),
                 "bound": "fp64 pipe (maximum-entropy Newton in FP64 in both precisions)"}
+            if dfma_peak:
+                out[f"c5_spray_2048_{precision}"]["roofline"] = fp64_roofline(
+                    f"spray step {precision}", 2048 * 2048 * 200 / sec, dfma_peak)
+            if g5 is not None and accuracy is not None:
+                s.set_state(pd, primitive=True)
+                s.run(int(g5["steps"]))
+                acc5[precision] = errors_vs(s.state().reshape(6, -1)[:, g5["flat_index"]], g5["W"])
+    if acc5:
+        accuracy["c5_spray_2048"] = dict(acc5, samples=int(len(g5["flat_index"])), steps=int(g5["steps"]),
+                                         against="stored oracle samples (tests/golden/c5_oracle_samples.npz)")
     if oracle_too:
         out["c5_spray_2048_f64"]["oracle"] = oracle_sample(d, prim, 2, "a sample (cold Newton starts)")
     del pd
@@ -478,6 +617,8 @@ def main():
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
+    choices = {}
+
     def time_jobs(precision, steps, warmup, clocks=False):
         s = fvlib.Solver(d, precision, stream=sptr, tune=args.tune)
         s.set_state(prim_dev, primitive=True)
@@ -497,6 +638,7 @@ def main():
         ck_res = ck.stop() if ck else None
         ms = max_over_ranks(ev0.elapsed_time(ev1), f"cuda:{local}")
         info = s.kernel_info()[1]
+        choices[precision] = s.kernel_choice()
         s.close()
         return ms, ck_res, info
 
@@ -509,6 +651,8 @@ def main():
 
     # ---- FP32-bulk headline
     ms32, clk, kinfo32 = time_jobs("f32", args.steps, args.warmup, clocks=(rank == 0))
+    # the step kernels of the region, and per job the one-warp read-back of
+    # the control block that fv_run ends with
     launches = args.steps * nsteps_job
     value32 = whole_job_throughput(ncell, nsteps_job, args.steps, ws, ms32)
     hbm, peak_kind = peaks()
@@ -521,35 +665,49 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": desc, "cells": ncell, "time_steps_per_bench_step": nsteps_job,
-                      "kernel": kinfo32, "l2": "inputs larger than L2 (state buffers 1 GiB f32 / 2 GiB f64)",
+                      "kernel": kinfo32, "kernel_choice": choices.get("f32"),
+                      "l2": "inputs larger than L2 (state buffers 1 GiB f32 / 2 GiB f64)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm, "unit": "GB/s",
-                        "frac": achieved32 / hbm,
+                        "frac": achieved32 / hbm, "frac_nominal": achieved32 / NOMINAL_HBM_GBS,
                         "traffic": (None if measured_traffic_per_cell(kinfo32) is None
                                     else measured_traffic_per_cell(kinfo32) * ncell),
                         "traffic_source": "ncu dram__bytes_read+write of one launch of this kernel on the 8192^2 workload",
                         "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                         "algorithmic_bytes_per_launch": algo_bytes_32,
                         "avg_launch_us": avg_launch_s * 1e6},
-           "gpu_launches": launches}
+           "gpu_launches": launches + args.steps}
     if clk:
         out["clocks"] = clk
 
     # ---- FP64 plain beside it
     if args.only == "f32":
         args.no_fp64 = args.no_e2e = args.no_cpu_baseline = args.no_extra = True
+    dfma_peak = None
     if not args.no_fp64:
+        dfma_peak = fvlib.fma_peak("f64", 0.05, sptr)
+        out["fp64_pipe_peak"] = {"dfma_per_s": dfma_peak, "tflops": 2 * dfma_peak / 1e12,
+                                 "ffma_per_s": fvlib.fma_peak("f32", 0.05, sptr),
+                                 "how": "fv_fma_peak: 8 blocks of 256 threads per SM, 8 independent FMA chains "
+                                        "per thread, best of 3 launches of ~50 ms, CUDA events"}
         k64 = max(1, min(args.steps, 2))
         ms64, _, kinfo64 = time_jobs("f64", k64, 1)
         value64 = whole_job_throughput(ncell, nsteps_job, k64, ws, ms64)
         algo64 = 2 * nvar * 8 * ncell
         avg64 = ms64 / 1e3 / (k64 * nsteps_job)
+        moved64 = (2 * 8 * 8 * ncell) if " pc" in kinfo64 else algo64
         out["fp64"] = {"value": value64, "unit": "cell-updates/s", "ms_per_step": ms64 / k64,
                        "steps": k64, "kernel": kinfo64,
                        "hbm_gbs_achieved": algo64 / avg64 / 1e9, "hbm_frac": algo64 / avg64 / 1e9 / hbm,
+                       "roofline": fp64_roofline(kinfo64, value64 / ws, dfma_peak),
+                       "traffic": {"algorithmic_bytes_per_cell_update": 2 * nvar * 8,
+                                   "moved_bytes_per_cell_update": moved64 // ncell,
+                                   "note": "the carried-primitive kernel (pc) stores u, v, p, c as four more "
+                                           "planes: 128 B moved per cell-update against the method's 64"},
                        "note": "FP64 arithmetic is bound by the FP64 pipe, not HBM"}
         out["fp32_speedup_vs_fp64"] = value32 / value64
-        out["fp64"]["gpu_launches"] = k64 * nsteps_job
+        out["fp64"]["gpu_launches"] = k64 * (nsteps_job + 1)
+        out["fp64"]["kernel_choice"] = choices.get("f64")
 
     # ---- bfloat16 storage (FP32 arithmetic), 16 B per cell-update
     if not args.no_fp64:
@@ -561,6 +719,7 @@ def main():
         out["bf16_storage"] = {"value": valueb, "unit": "cell-updates/s", "ms_per_step": msb / kb, "steps": kb,
                                "kernel": kinfob, "hbm_gbs_achieved": algob / avgb / 1e9,
                                "hbm_frac": algob / avgb / 1e9 / hbm,
+                               "kernel_choice": choices.get("bf16"),
                                "note": "bfloat16 state, FP32 arithmetic, FP64 dt/t/totals; accuracy below"}
 
     # ---- end to end through the C ABI with host buffers
@@ -575,7 +734,7 @@ def main():
         s.run(nsteps_job)
         s.snapshot(h_out)
         s.snapshot_wait()
-        k = max(2, min(args.steps, 8))
+        k = max(20, args.steps)
         # each job: its input copied in from pinned host memory, nsteps_job
         # steps, its result copied out to pinned host memory.  The copy in of
         # job j+1 (fv_prefetch_state) and the copy out of job j (fv_snapshot)
@@ -602,12 +761,14 @@ def main():
                       "path": "fv_prefetch_state(pinned host f32 primitive, asynchronous, overlapping the previous "
                               "job) + fv_set_state_prefetched + fv_run + fv_snapshot(pinned host f32, "
                               "asynchronous, overlapping the next job) + fv_snapshot_wait; host wall clock"}
-        out["e2e"]["gpu_launches"] = k * (nsteps_job + 3)
+        # per job: load, wave-speed seed and control read-back (set_state_prefetched),
+        # the steps and a read-back (fv_run), a read-back and the staging copy (fv_snapshot)
+        out["e2e"]["gpu_launches"] = k * (nsteps_job + 6)
 
     # ---- accuracy of the timed configuration against stored oracle samples
-    golden = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle_samples.npz")
-    if os.path.exists(golden):
-        g = np.load(golden)
+    accuracy = {}
+    g = golden_samples(args.workload)
+    if g is not None:
         acc = {}
         for precision in ("f32", "f64", "bf16"):
             s = fvlib.Solver(d, precision, stream=sptr)
@@ -615,17 +776,18 @@ def main():
             s.run(int(g["steps"]))
             W = s.state()
             s.close()
-            idx = g["flat_index"]
-            got = W.reshape(W.shape[0], -1)[:, idx]
-            ref = g["W"]
-            l1 = (np.abs(got - ref).sum(axis=1) / np.abs(ref).sum(axis=1)).tolist()
-            linf = (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).tolist()
-            acc[precision] = {"rel_l1": l1, "rel_linf": linf}
-        out["accuracy_vs_oracle"] = dict(acc, samples=int(len(g["flat_index"])), steps=int(g["steps"]))
+            acc[precision] = errors_vs(W.reshape(W.shape[0], -1)[:, g["flat_index"]], g["W"])
+        accuracy[WORKLOAD_KEYS.get(args.workload, args.workload)] = dict(
+            acc, samples=int(len(g["flat_index"])), steps=int(g["steps"]),
+            against=f"stored oracle samples (tests/golden/{args.workload}_oracle_samples.npz)")
 
     if not args.no_extra and args.workload == "c3":
         out["other_workloads"] = secondary_workloads(fvlib, torch, sptr, local, hbm,
-                                                     oracle_too=(rank == 0 and not args.no_cpu_baseline and ws == 1))
+                                                     oracle_too=(rank == 0 and not args.no_cpu_baseline and ws == 1),
+                                                     accuracy=accuracy, dfma_peak=dfma_peak)
+    if accuracy:
+        out["accuracy_vs_oracle"] = dict(accuracy, norms="per variable: rel_l1 = sum|gpu-oracle| / sum|oracle|, "
+                                                          "rel_linf = max|gpu-oracle| / max|oracle|")
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline_run(args.workload, d, prim)

@@ -81,8 +81,11 @@ enum { FV_CONSERVED = 0, FV_PRIMITIVE = 1 };
  *   fixed_dt > 0: the paper's constant dt, checked against Eq. (CFL_cond)
  *     at the start of every step (FV_ERR_CFL on violation).
  *   stream: cudaStream_t on which all work is queued (NULL: legacy stream).
- *   tune: 0 = stored kernel choice, 1 = time the candidates at the first
- *     run and keep the fastest, >= 2: force candidate (tune - 2). */
+ *   tune: 0 = the kernel the autotuner's recorded table names for this
+ *     (system, precision, grid-size class, mode), or the occupancy
+ *     heuristic where the table has no entry (fv_kernel_choice says which);
+ *     1 = time the candidates at the first run and keep the fastest;
+ *     >= 2: force candidate (tune - 2). */
 typedef struct fv_config {
   int nx, ny, npart_x, npart_y;
   double xmin, xmax, ymin, ymax;
@@ -250,15 +253,44 @@ const char *fv_kernel_info_two_step(const fv_ctx *ctx);
  * forces that candidate; tune = 1 times them all on the first fv_run. */
 fv_status fv_kernel_candidate(int system, int precision, int index, const char **desc);
 
+/* How the step kernel that fv_kernel_info names (two_step = 0), or the
+ * two-step kernel (two_step != 0, FV_ERR_STATE when two steps per pass are
+ * off), was chosen.  With fv_config.tune = 0 the library looks the
+ * (system, precision, grid-size class, mode) key up in the table of choices
+ * the autotuner recorded on a GB300 (python -m paper_1701_05431_gb300.autotune
+ * times every candidate on a seeded workload of each measured class and
+ * compiles the fastest into the library); *how is then "table: <key>
+ * (<workload>, <rate> G cell-updates/s when recorded)".  Keys the table
+ * lacks take the occupancy heuristic ("heuristic ...": the first candidate,
+ * in order of preference, whose warp tasks fill the GPU).  tune = 1 gives
+ * "autotuned ..." and tune >= 2 "forced ...".  Grid-size classes by cell
+ * count: 0 below 2^16, 1 below 2^20, 2 below 2^24, 3 from 2^24 on.  The
+ * string lives until the next call on the context. */
+fv_status fv_kernel_choice(const fv_ctx *ctx, int two_step, const char **how);
+
 /* Q-point Gauss-Legendre nodes x[Q] and weights w[Q] on [0,1] used by the
  * spray source's maximum-entropy quadrature (Sec. 6.2), as computed by the
  * library on the host.  1 <= Q <= 128. */
 fv_status fv_gauss_legendre(int Q, double *x, double *w);
 
+/* Measured FMA throughput of the current GPU (the denominator of the
+ * arithmetic roofline).  The FP64 Euler step and the spray source step
+ * (Sec. 6.2) are bound by the FP64 pipe rather than by HBM, so their
+ * roofline fraction is the FP64 work they retire per second over this rate.
+ * precision FV_F64 (DFMA) or FV_F32 (FFMA).  Every thread of a full grid
+ * (8 blocks of 256 threads per SM) runs four, then eight, independent
+ * a = a*b + c chains with register operands and no memory traffic; for each,
+ * after a calibration launch, three launches of about `seconds` each
+ * (0.001 <= seconds <= 2) are timed with CUDA events on `stream`, and
+ * *fma_per_s receives the best of the six: thread-level FMA instructions
+ * retired per second (FLOP/s = 2 x that).  Synchronises the stream;
+ * allocates no device memory. */
+fv_status fv_fma_peak(int precision, double seconds, double *fma_per_s, void *stream);
+
 /* No-allocation totals.  The paper has no counterpart: this entry point is
- * for callers that must not let the library allocate device memory (work
- * enqueued while their stream is captured into a CUDA graph, loops that
- * forbid allocator calls, frameworks that own all device memory).  Same
+ * for callers that cannot let the library allocate device memory (loops that
+ * forbid allocator calls and the synchronisation they cause, frameworks that
+ * own all device memory and account for every byte).  Same
  * per-variable totals sum_ij W_v * cell_area as fv_totals, for a caller-owned
  * device state of nvar x ny x nx values of dtype (FV_F64 or FV_F32, layout
  * above), written as nvar doubles to the caller's device buffer `totals`,
@@ -269,7 +301,9 @@ fv_status fv_gauss_legendre(int Q, double *x, double *w);
  * fv_last_error(NULL)).  The first call on a device looks up that array's
  * device address with the device current; make that first call before any
  * stream capture.  All calls on a device share the array: calls that overlap
- * on the GPU race and must be ordered by the caller. */
+ * on the GPU race and must be ordered by the caller.  The looked-up address
+ * is kept for the life of the process; after a cudaDeviceReset it no longer
+ * names the array, so calls after a reset are not supported. */
 fv_status fv_totals_noalloc(const void *state, int dtype, int nvar, int nx, int ny, double cell_area,
                             double *totals, void *stream);
 
@@ -333,6 +367,10 @@ fv_status fv_batch_set_wait_limit(fv_batch *b, double seconds, int never_release
  * for every instance (FV_ERR_INVALID_ARG otherwise); FV_ERR_OOM if the copy
  * cannot be allocated. */
 fv_status fv_batch_set_dataflow(fv_batch *b, int on);
+
+/* How the batched kernel was chosen, as fv_kernel_choice describes it (the
+ * table is keyed by the cells of all instances together, mode "batched"). */
+fv_status fv_batch_kernel_choice(const fv_batch *b, const char **how);
 
 /* Detail of the last failure on this batch ("" if none). */
 const char *fv_batch_last_error(const fv_batch *b);

@@ -27,8 +27,7 @@
  * Each cell's residual is the same expression of its four face fluxes in
  * both modes, so the two agree bit for bit.
  *
- * Readings taken where the paper is silent or garbled (also listed in the
- * design notes):
+ * Readings taken where the paper is silent or garbled:
  *   - residual sign follows Eq. (VF_scheme): RHS = -dt/dx (Fe - Fw)
  *     - dt/dy (Fn - Fs) (Eq. (RHSFilling) prints the opposite sign);
  *   - the flux is the local Lax-Friedrichs (Rusanov) flux, sigma evaluated

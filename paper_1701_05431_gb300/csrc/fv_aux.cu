@@ -211,6 +211,21 @@ __global__ void seed_lambda_kernel(const typename Ops<A>::S *__restrict__ state,
   }
 }
 
+// The control block copied by one warp into host memory mapped for the
+// device (its 8-byte words, one per lane).
+__global__ void ctrl_readback_kernel(const Ctrl *__restrict__ src, Ctrl *dst) {
+  constexpr int words = (int)(sizeof(Ctrl) / sizeof(unsigned long long));
+  static_assert(sizeof(Ctrl) % sizeof(unsigned long long) == 0 && words <= 32, "control block of 8-byte words");
+  const int l = threadIdx.x;
+  if (l < words)
+    reinterpret_cast<volatile unsigned long long *>(dst)[l] = __ldcg(reinterpret_cast<const unsigned long long *>(src) + l);
+}
+
+cudaError_t launch_ctrl_readback(const Ctrl *src, Ctrl *dst_mapped, cudaStream_t s) {
+  ctrl_readback_kernel<<<1, 32, 0, s>>>(src, dst_mapped);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_seed_lambda(int system, int prec, const void *state, int nx, int ny,
                                long long pitch, long long plane, double p0, double p1, Ctrl *ctrl,
                                int slot, cudaStream_t s) {

@@ -43,6 +43,7 @@
 
 #include "../../include/fv.h"
 #include "fv_internal.h"
+#include "fv_tune.h"
 #include "fv_step.cuh"
 
 namespace fv {
@@ -369,6 +370,7 @@ struct fv_batch {
   long long timeout_ns = 2000000000LL;
   int skip_release = -1;
   bool tuned = false;
+  std::string choice;          // how the kernel was chosen (fv_batch_kernel_choice)
   int dataflow = 0;
   RunInfo *info = nullptr, *h_info = nullptr;  // per instance, device and pinned host
   char *ckpt = nullptr;                        // dataflow: every instance's state at run start
@@ -618,12 +620,25 @@ extern "C" fv_status fv_batch_init(const fv_config *cfgs, int n, fv_batch **out)
     return FV_ERR_INVALID_ARG;
   }
   vi = cand[0];
+  b->choice = cfgs[0].tune == 1 ? "autotuned: the fastest candidate on one timed step before the first run"
+                                : "heuristic (no table entry): the first candidate";
+  if (cfgs[0].tune == 0) {
+    long long cells = 0;
+    for (int k = 0; k < n; ++k) cells += (long long)cfgs[k].nx * cfgs[k].ny;
+    if (const TuneEntry *te = tune_lookup(b->system, b->prec, cells, kTuneBatch))
+      for (int k : cand)
+        if (std::string(vs[k].desc) == te->kernel) {
+          vi = k;
+          b->choice = tune_describe(*te);
+        }
+  }
   if (cfgs[0].tune >= 2) {
     if (cfgs[0].tune - 2 >= (int)cand.size()) {
       fv_batch_destroy(b);
       return FV_ERR_INVALID_ARG;
     }
     vi = cand[cfgs[0].tune - 2];
+    b->choice = "forced: candidate " + std::to_string(cfgs[0].tune - 2);
   }
   fv_status st = batch_select(b, vi);
   if (st != FV_OK) {
@@ -1019,6 +1034,12 @@ extern "C" fv_status fv_batch_kernel_info(fv_batch *b, int *variant, const char 
     *variant = idx;
   }
   if (desc) *desc = V.desc;
+  return FV_OK;
+}
+
+extern "C" fv_status fv_batch_kernel_choice(const fv_batch *b, const char **how) {
+  if (!b || !how) return FV_ERR_INVALID_ARG;
+  *how = b->choice.c_str();
   return FV_OK;
 }
 

@@ -16,6 +16,7 @@
 
 #include "../../include/fv.h"
 #include "fv_internal.h"
+#include "fv_tune.h"
 #include "fv_step.cuh"
 #include "fv_tb.cuh"
 
@@ -66,7 +67,8 @@ struct fv_ctx {
   int ovl_task = 0;
   void *buf[2] = {nullptr, nullptr};
   Ctrl *ctrl = nullptr;
-  Ctrl *h_ctrl = nullptr;        // pinned mirror
+  Ctrl *h_ctrl = nullptr;        // pinned mirror, mapped for the device
+  Ctrl *h_ctrl_dev = nullptr;    // its device address
   double *h_scalar = nullptr;    // pinned scratch for small uploads
   void *staging = nullptr;
   size_t staging_bytes = 0;
@@ -97,6 +99,10 @@ struct fv_ctx {
   int variant = -1;
   int grid = 0;
   int ty = 0;                    // rows per warp task of the selected kernel
+  std::string choice;            // how that kernel was chosen (fv_kernel_choice)
+  std::string tb_choice;         // how the two-step kernel was chosen
+  int single_variant = -1;       // the two-buffer kernel (restored when in-place mode ends)
+  std::string single_choice;
   std::string desc;              // its description with the task rows
   double dx = 0, dy = 0;
   std::map<int, cudaGraphExec_t> graphs;
@@ -273,6 +279,27 @@ static std::vector<int> candidates(int system, int prec) {
     if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace && !vs[k].tb) out.push_back((int)k);
   return out;
 }
+
+// The variant the recorded table names for this key (mode: TuneMode), or -1;
+// *how receives the table entry's description.
+static int table_variant(int system, int prec, int nx, int ny, int mode, std::string *how) {
+  const TuneEntry *e = tune_lookup(system, prec, (long long)nx * ny, mode);
+  if (!e) return -1;
+  const auto &vs = all_variants();
+  for (size_t k = 0; k < vs.size(); ++k) {
+    const Variant &V = vs[k];
+    if (V.system != system || V.precision != prec || V.inplace != (mode == kTuneInplace ? 1 : 0) ||
+        V.tb != (mode == kTuneTwoStep ? 2 : 0))
+      continue;
+    if (std::string(V.desc) == e->kernel) {
+      if (how) *how = tune_describe(*e);
+      return (int)k;
+    }
+  }
+  return -1;
+}
+
+static const char *kHeuristic = "heuristic (no table entry): the first candidate whose warp tasks fill the GPU";
 
 static void free_graphs(fv_ctx *c) {
   for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -462,8 +489,13 @@ static fv_status get_graph(fv_ctx *c, int nsteps, cudaGraphExec_t *out, bool pas
   return FV_OK;
 }
 
+// Read the control block back after the work queued on the stream.  A
+// kernel writes it into the mapped host mirror: a device-to-host memcpy of
+// its 72 bytes would wait on the copy engine behind large copies other
+// streams have running (an asynchronous snapshot of the state took 3.5 ms of
+// the next job's load that way).
 static fv_status read_ctrl(fv_ctx *c) {
-  FV_CUDA(c, cudaMemcpyAsync(c->h_ctrl, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  FV_CUDA(c, launch_ctrl_readback(c->ctrl, c->h_ctrl_dev, c->stream));
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
   return FV_OK;
 }
@@ -512,7 +544,10 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
   for (int b = 0; b < 2; ++b)
     if ((e = cudaMalloc(&c->buf[b], c->buf_bytes)) != cudaSuccess) return bail(e, "cudaMalloc(state)");
   if ((e = cudaMalloc(&c->ctrl, sizeof(Ctrl))) != cudaSuccess) return bail(e, "cudaMalloc(ctrl)");
-  if ((e = cudaMallocHost(&c->h_ctrl, sizeof(Ctrl))) != cudaSuccess) return bail(e, "cudaMallocHost");
+  if ((e = cudaHostAlloc(&c->h_ctrl, sizeof(Ctrl), cudaHostAllocMapped)) != cudaSuccess)
+    return bail(e, "cudaHostAlloc(ctrl mirror)");
+  if ((e = cudaHostGetDevicePointer(&c->h_ctrl_dev, c->h_ctrl, 0)) != cudaSuccess)
+    return bail(e, "cudaHostGetDevicePointer(ctrl mirror)");
   if ((e = cudaMallocHost(&c->h_scalar, 64)) != cudaSuccess) return bail(e, "cudaMallocHost");
   const int nb = totals_blocks(cfg->ny);
   if ((e = cudaMalloc(&c->partials, sizeof(double) * 2 * 8 * nb)) != cudaSuccess)
@@ -559,7 +594,12 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     cudaFree(d_bc);
   }
   int prec = cfg->precision;  // 0 f64, 1 f32, 2 bf16 storage
-  int vi = default_variant_for(cfg->system, prec, cfg->nx, cfg->ny, c->sms);
+  int vi = cfg->tune == 0 ? table_variant(cfg->system, prec, cfg->nx, cfg->ny, kTuneSingle, &c->choice) : -1;
+  if (vi < 0) {
+    vi = default_variant_for(cfg->system, prec, cfg->nx, cfg->ny, c->sms);
+    c->choice = cfg->tune == 1 ? "autotuned: the fastest candidate on one timed step before the first run"
+                               : kHeuristic;
+  }
   if (cfg->tune >= 2) {
     auto cand = candidates(cfg->system, prec);
     if (cfg->tune - 2 >= (int)cand.size()) {
@@ -567,6 +607,7 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
       return fail(nullptr, FV_ERR_INVALID_ARG, "tune index out of range");
     }
     vi = cand[cfg->tune - 2];
+    c->choice = "forced: candidate " + std::to_string(cfg->tune - 2);
   }
   if (vi < 0) {
     fv_destroy(c);
@@ -578,6 +619,8 @@ extern "C" fv_status fv_init(const fv_config *cfg, fv_ctx **out) {
     fv_destroy(c);
     return st;
   }
+  c->single_variant = vi;
+  c->single_choice = c->choice;
   *out = c;
   return FV_OK;
 }
@@ -902,6 +945,7 @@ static fv_status autotune(fv_ctx *c) {
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
   if (st != FV_OK) return st;
   c->tuned = true;
+  c->single_variant = best;
   return select_variant(c, best);
 }
 
@@ -982,7 +1026,11 @@ extern "C" fv_status fv_set_time_blocking(fv_ctx *c, int steps_per_pass) {
   for (int s = 0; s < 4; ++s)
     if (c->cfg.bc[s] != FV_BC_PERIODIC) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass need a periodic grid");
   if (c->inplace) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass do not run in place");
-  int vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 0, 2);
+  std::string how = kHeuristic;
+  int vi = c->cfg.tune == 0
+               ? table_variant(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, kTuneTwoStep, &how)
+               : -1;
+  if (vi < 0) vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 0, 2);
   if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "no two-step kernel for this system and precision");
   if (c->cfg.tune >= 2) {
     // a forced candidate: the (tune - 2)-th two-step kernel of (system, precision)
@@ -996,6 +1044,7 @@ extern "C" fv_status fv_set_time_blocking(fv_ctx *c, int steps_per_pass) {
         break;
       }
     if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "tune index out of range for two-step kernels");
+    how = "forced: two-step candidate " + std::to_string(c->cfg.tune - 2);
   }
   const Variant &V = all_variants()[vi];
   if (V.smem > 0)
@@ -1008,6 +1057,7 @@ extern "C" fv_status fv_set_time_blocking(fv_ctx *c, int steps_per_pass) {
   if (need < grid) grid = need;
   c->tb_variant = vi;
   c->tb_grid = (int)(grid < 1 ? 1 : grid);
+  c->tb_choice = how;
   free_graphs(c);
   return FV_OK;
 }
@@ -1142,7 +1192,11 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
   }
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
   if (on) {
-    int vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 1);
+    std::string how = kHeuristic;
+    int vi = c->cfg.tune == 0
+                 ? table_variant(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, kTuneInplace, &how)
+                 : -1;
+    if (vi < 0) vi = default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms, 1);
     if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "no in-place kernel for this system and precision");
     if (c->cfg.tune >= 2) {
       // a forced candidate: the (tune - 2)-th in-place kernel of (system, precision)
@@ -1156,6 +1210,7 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
           break;
         }
       if (vi < 0) return fail(c, FV_ERR_INVALID_ARG, "tune index out of range for in-place kernels");
+      how = "forced: in-place candidate " + std::to_string(c->cfg.tune - 2);
     }
     const Variant &V = all_variants()[vi];
     const int sw = 30 * V.V;
@@ -1180,6 +1235,7 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
     c->ovl_parity_bytes = pb;
     c->ovl_task = ts;
     c->inplace = true;
+    c->choice = how;
     fv_status st = select_variant(c, vi);
     if (st != FV_OK) return st;
     if (c->has_state) {
@@ -1204,7 +1260,19 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
   c->ovl_parity_bytes = 0;
   c->ovl_task = 0;
   c->inplace = false;
-  return select_variant(c, default_variant_for(c->cfg.system, c->cfg.precision, c->cfg.nx, c->cfg.ny, c->sms));
+  c->choice = c->single_choice;
+  return select_variant(c, c->single_variant);
+}
+
+extern "C" fv_status fv_kernel_choice(const fv_ctx *c, int two_step, const char **how) {
+  if (!c || !how) return FV_ERR_INVALID_ARG;
+  if (two_step) {
+    if (c->tb_variant < 0) return fail(const_cast<fv_ctx *>(c), FV_ERR_STATE, "two steps per pass are off");
+    *how = c->tb_choice.c_str();
+  } else {
+    *how = c->choice.c_str();
+  }
+  return FV_OK;
 }
 
 extern "C" fv_status fv_kernel_candidate(int system, int precision, int index, const char **desc) {

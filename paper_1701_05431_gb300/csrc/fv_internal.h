@@ -48,6 +48,10 @@ cudaError_t launch_totals(int prec, int nvar, const void *state, int nx, int ny,
                           long long plane, double *partials, int nblocks, double *out,
                           double cell_area, cudaStream_t s);
 int totals_blocks(int ny);
+// Copy the control block into host memory mapped for the device, by a kernel
+// on stream s (no copy engine: a small device-to-host copy would queue behind
+// large copies already running on the engine, such as a snapshot's).
+cudaError_t launch_ctrl_readback(const Ctrl *src, Ctrl *dst_mapped, cudaStream_t s);
 // FP64 Euler with carried primitives: planes 4..7 (u, v, p, c) of a state
 // from its planes 0..3, and the same of the four boundary states (bc_dev:
 // 4 x 8 doubles, out_dev: 4 x 4 doubles).

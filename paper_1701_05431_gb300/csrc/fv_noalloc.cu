@@ -1,9 +1,7 @@
 // fv_noalloc.cu -- conservation totals of a caller-owned state with no device
 // allocation by the library.
 //
-// Some callers must not let a library allocate device memory: code that
-// enqueues work while its stream is being captured into a CUDA graph (an
-// allocation there either fails or breaks the capture), real-time or
+// Some callers cannot let a library allocate device memory: real-time or
 // latency-bound loops that forbid allocator calls and the synchronisation
 // cudaMalloc/cudaFree can cause, and frameworks that hand all device memory
 // out of their own pool and account for every byte.  fv_totals_noalloc
@@ -18,7 +16,9 @@
 // partial sum before reading it back, so nothing needs clearing between
 // calls.  Two calls whose work overlaps on the GPU (for example on two
 // streams with no ordering between them) race on the array: the caller must
-// order them.
+// order them.  The array's device address is looked up once per device and
+// kept; a cudaDeviceReset destroys the context that address belongs to, so
+// calling this entry point after one in the same process is not supported.
 #include <cuda_runtime.h>
 
 #include <mutex>

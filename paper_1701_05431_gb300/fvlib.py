@@ -111,6 +111,10 @@ def load(build_if_missing: bool = True):
     L.fv_totals_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, vp, vp]
     L.fv_totals_noalloc.restype = ctypes.c_int
+    L.fv_kernel_choice.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p)]
+    L.fv_kernel_choice.restype = ctypes.c_int
+    L.fv_fma_peak.argtypes = [ctypes.c_int, ctypes.c_double, dp, vp]
+    L.fv_fma_peak.restype = ctypes.c_int
     _declare_batch(L)
     _lib = L
     return L
@@ -136,6 +140,8 @@ def _declare_batch(L):
     L.fv_batch_last_error.restype = ctypes.c_char_p
     L.fv_batch_kernel_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_char_p)]
     L.fv_batch_kernel_info.restype = ctypes.c_int
+    L.fv_batch_kernel_choice.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p)]
+    L.fv_batch_kernel_choice.restype = ctypes.c_int
     L.fv_batch_set_wait_limit.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.fv_batch_set_wait_limit.restype = ctypes.c_int
     L.fv_batch_set_dataflow.argtypes = [vp, ctypes.c_int]
@@ -340,6 +346,13 @@ class Solver:
         _check(self.lib.fv_lambda_max(self.ctx, ctypes.byref(out)), self.ctx, self.lib)
         return out.value
 
+    def kernel_choice(self, two_step: bool = False) -> str:
+        """How the step kernel (or the two-step kernel) was chosen: the
+        recorded table entry, the heuristic, autotuning or a forced index."""
+        h = ctypes.c_char_p()
+        _check(self.lib.fv_kernel_choice(self.ctx, 1 if two_step else 0, ctypes.byref(h)), self.ctx, self.lib)
+        return h.value.decode()
+
     def kernel_info(self):
         v = ctypes.c_int(0)
         d = ctypes.c_char_p()
@@ -355,6 +368,15 @@ def totals_noalloc(state, totals, cell_area: float, stream: int = 0) -> int:
     p, dev = _ptr(state)
     q, _ = _ptr(totals)
     return L.fv_totals_noalloc(p, _dtype_code(state), int(nvar), int(nx), int(ny), float(cell_area), q, stream)
+
+
+def fma_peak(precision: str = "f64", seconds: float = 0.05, stream: int = 0) -> float:
+    """Measured FMA instructions retired per second by the GPU's FP64
+    (precision "f64") or FP32 ("f32") pipe: fv_fma_peak."""
+    L = load()
+    r = ctypes.c_double(0)
+    _check(L.fv_fma_peak(PRECISIONS[precision], float(seconds), ctypes.byref(r), stream), None, L)
+    return r.value
 
 
 def kernel_candidates(system: str, precision: str):
@@ -445,6 +467,11 @@ class Batch:
         s = ctypes.c_longlong(0)
         self._check(self.lib.fv_batch_time(self.b, int(k), ctypes.byref(t), ctypes.byref(s)))
         return t.value, s.value
+
+    def kernel_choice(self) -> str:
+        h = ctypes.c_char_p()
+        self._check(self.lib.fv_batch_kernel_choice(self.b, ctypes.byref(h)))
+        return h.value.decode()
 
     def kernel_info(self):
         v = ctypes.c_int(0)

@@ -98,3 +98,27 @@ def test_null_arguments():
     assert L.fv_run(None, 1, 0.0, None) == fvlib.FV_ERR_INVALID_ARG
     assert L.fv_set_state(None, None, 0, 0, 0) == fvlib.FV_ERR_INVALID_ARG
     L.fv_destroy(None)
+
+
+def test_fma_peak_rejects_bad_arguments_before_any_cuda_call():
+    L = fvlib.load()
+    r = ctypes.c_double(0)
+    assert L.fv_fma_peak(7, 0.05, ctypes.byref(r), None) == fvlib.FV_ERR_INVALID_ARG
+    assert L.fv_fma_peak(0, 10.0, ctypes.byref(r), None) == fvlib.FV_ERR_INVALID_ARG
+    assert L.fv_fma_peak(0, 0.05, None, None) == fvlib.FV_ERR_INVALID_ARG
+
+
+def test_recorded_kernel_table_names_compiled_candidates():
+    """Every two-buffer entry of the autotuner's table names a candidate the
+    library has compiled (a stale table would silently fall back)."""
+    path = os.path.join(ROOT, "paper_1701_05431_gb300", "tune_table.json")
+    if not os.path.exists(path):
+        pytest.skip("no autotune table recorded")
+    import json
+    from paper_1701_05431_gb300 import autotune
+    for r in json.load(open(path)):
+        assert r["size_class"] == autotune.size_class(r["cells"])
+        if r["mode"] == "single":
+            names = fvlib.kernel_candidates(r["system"], r["precision"])
+            for kernel, _ in r["candidates"]:
+                assert kernel in names, (r["name"], kernel)

@@ -1,9 +1,8 @@
 """fv_totals_noalloc: the conservation totals for callers that cannot let the
-library allocate device memory (work queued while a stream is captured into a
-CUDA graph, loops that forbid allocator calls, frameworks that own all device
-memory).  It must return what the allocating entry point fv_totals returns,
-call after call, while keeping its partial sums in the library's fixed device
-array.
+library allocate device memory (loops that forbid allocator calls, frameworks
+that own all device memory).  It must return what the allocating entry point
+fv_totals returns, call after call, while keeping its partial sums in the
+library's fixed device array.
 
 This file is collected last on purpose, so that a run stopping at its first
 failure has already run every other test; it passes alone in a fresh
