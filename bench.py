@@ -414,6 +414,26 @@ def secondary_workloads(fvlib, torch, sptr, local, hbm, oracle_too=False, accura
                 "hbm_gbs_algorithmic": nb / sec / 1e9, "kernel": s.kernel_info()[1],
                 "kernel_choice": s.kernel_choice(),
                 "note": "job = set_state from device + 500 steps; 134 MB/268 MB state, close to L2 size"}
+    # the same grid in the paper's fixed-dt mode, dt = 0.4 min(dx, dy) / lmax(W^0):
+    # one step per launch, and two steps per launch (transmissive ghosts of the
+    # intermediate state inside the pass)
+    lam0 = float(np.max(np.maximum(np.abs(prim[1]), np.abs(prim[2])) + np.sqrt(1.4 * prim[3] / prim[0])))
+    dfix2 = dict(d, fixed_dt=0.4 * min(1.0 / d["nx"], 1.0 / d["ny"]) / lam0)
+    for passes in (1, 2):
+        with fvlib.Solver(dfix2, "f32", stream=sptr) as s:
+            if passes == 2:
+                s.set_time_blocking(2)
+
+            def job():
+                s.set_state(pd, primitive=True)
+                s.run(500)
+            sec = timed(job, 1)
+            name = "two_steps_per_launch" if passes == 2 else "per_step_launches"
+            out[f"c2_fixed_dt_{name}_f32"] = {
+                "cell_updates_per_s": 2048 * 2048 * 500 / sec, "ms_per_job": sec * 1e3,
+                "kernel": s.two_step_kernel() if passes == 2 else s.kernel_info()[1],
+                "kernel_choice": s.kernel_choice(two_step=(passes == 2)),
+                "note": "four-quadrant 2048^2, transmissive, fixed dt; job = set_state from device + 500 steps"}
     if acc2:
         accuracy["c2_four_quadrant_2048"] = dict(acc2, samples=int(len(g2["flat_index"])), steps=500,
                                                  against="stored oracle samples (tests/golden/c2_oracle_samples.npz)")

@@ -153,9 +153,11 @@ fv_status fv_get_state(fv_ctx *ctx, void *dst, int dst_is_device, int dst_dtype)
 
 /* Time blocking: steps_per_pass = 2 advances two time steps per kernel
  * launch, reading and writing the state once per two steps (half the bytes
- * per cell-update).  Needs the paper's fixed dt (fixed_dt > 0, Sec. 2.2.1)
- * and periodic boundaries on all four sides, advection or Euler, not in
- * place.  Results, times, step counts and errors are bit for bit those of
+ * per cell-update).  Needs the paper's fixed dt (fixed_dt > 0, Sec. 2.2.1),
+ * advection or Euler, not in place; any boundary conditions (on a
+ * transmissive or Dirichlet side the ghosts of the intermediate state take
+ * the boundary condition inside the pass).  Results, times, step counts and
+ * errors are bit for bit those of
  * one step per launch: a pass that finds the intermediate state failing the
  * paper's check dt lmax <= min(dx, dy) (or inadmissible) leaves everything
  * as it was and the steps from there run one at a time.  fv_run uses passes

@@ -60,6 +60,7 @@ struct fv_ctx {
   // two time steps per launch (fixed dt, periodic): its kernel and grid
   int tb_variant = -1;
   int tb_grid = 0;
+  bool tb_np = false;            // some side is not periodic: the two-step kernel's ghost-handling build
   // in-place mode: buf[1] == buf[0], overlap strips of the two parities
   bool inplace = false;
   void *ovl = nullptr;
@@ -443,19 +444,20 @@ static fv_status launch_step(fv_ctx *c, cudaStream_t s) {
 static fv_status launch_tb(fv_ctx *c, cudaStream_t s) {
   const Variant &V = all_variants()[c->tb_variant];
   dim3 grid(c->tb_grid), block(V.NW * 32);
+  const void *k = c->tb_np ? V.kernel_np : V.kernel;
   cudaError_t e;
   if (V.precision == 0) {
     StepArgs<double> a = make_args<double>(c, V);
     void *args[] = {&a};
-    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
+    e = cudaLaunchKernel(k, grid, block, args, V.smem, s);
   } else if (V.precision == 1) {
     StepArgs<float> a = make_args<float>(c, V);
     void *args[] = {&a};
-    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
+    e = cudaLaunchKernel(k, grid, block, args, V.smem, s);
   } else {
     StepArgs<__nv_bfloat16> a = make_args<__nv_bfloat16>(c, V);
     void *args[] = {&a};
-    e = cudaLaunchKernel(V.kernel, grid, block, args, V.smem, s);
+    e = cudaLaunchKernel(k, grid, block, args, V.smem, s);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "two-step kernel launch");
   return FV_OK;
@@ -1023,8 +1025,6 @@ extern "C" fv_status fv_set_time_blocking(fv_ctx *c, int steps_per_pass) {
   }
   if (steps_per_pass != 2) return fail(c, FV_ERR_INVALID_ARG, "steps per pass must be 1 or 2");
   if (!(c->cfg.fixed_dt > 0.0)) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass need the fixed-dt mode");
-  for (int s = 0; s < 4; ++s)
-    if (c->cfg.bc[s] != FV_BC_PERIODIC) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass need a periodic grid");
   if (c->inplace) return fail(c, FV_ERR_INVALID_ARG, "two steps per pass do not run in place");
   std::string how = kHeuristic;
   int vi = c->cfg.tune == 0
@@ -1047,16 +1047,21 @@ extern "C" fv_status fv_set_time_blocking(fv_ctx *c, int steps_per_pass) {
     how = "forced: two-step candidate " + std::to_string(c->cfg.tune - 2);
   }
   const Variant &V = all_variants()[vi];
+  bool np = false;
+  for (int s2 = 0; s2 < 4; ++s2) np |= c->cfg.bc[s2] != FV_BC_PERIODIC;
+  const void *kern = np ? V.kernel_np : V.kernel;
+  if (!kern) return fail(c, FV_ERR_INVALID_ARG, "no two-step kernel for this system and precision");
   if (V.smem > 0)
-    FV_CUDA(c, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
+    FV_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
   int nb = 0;
-  FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));
+  FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, V.NW * 32, V.smem));
   if (nb < 1) return fail(c, FV_ERR_CUDA, std::string("kernel cannot launch: ") + V.desc);
   const long long ntasks = (long long)((c->cfg.nx + 30 * V.V - 1) / (30 * V.V)) * ((c->cfg.ny + V.TY - 1) / V.TY);
   long long grid = (long long)nb * c->sms, need = (ntasks + V.NW - 1) / V.NW;
   if (need < grid) grid = need;
   c->tb_variant = vi;
   c->tb_grid = (int)(grid < 1 ? 1 : grid);
+  c->tb_np = np;
   c->tb_choice = how;
   free_graphs(c);
   return FV_OK;

@@ -26,11 +26,13 @@ struct Variant {
   int inplace;     // 1: in-place kernel (one state buffer plus overlap strips)
   int tb;          // 2: two time steps per launch (fixed dt, periodic); 0: one
   int carry = 0;   // 1: FP64 Euler with carried primitives (planes 4..7 of the state)
+  const void *kernel_np = nullptr;  // two-step kernels: the build for grids with a non-periodic side
 };
 
 // Registration hooks, one per translation unit of step kernels.
 void register_step_advection(std::vector<Variant> &out);
 void register_step_euler(std::vector<Variant> &out);
+void register_step_euler_tb(std::vector<Variant> &out);
 void register_step_spray(std::vector<Variant> &out);
 
 const std::vector<Variant> &all_variants();

@@ -29,6 +29,8 @@
 // launches advances any number of steps from any starting step.
 #pragma once
 
+#include <type_traits>
+
 #include "fv_device.cuh"
 
 namespace fv {
@@ -215,10 +217,16 @@ static __device__ __forceinline__ void load_row(const G &a,
   int dir;
   const int sj = row_src(a, j, dir);
   if (dir >= 0) {
+    // the prescribed state in the storage type, as every other loader and
+    // the ghost columns below give it (bfloat16 storage rounds it)
 #pragma unroll
-    for (int c = 0; c < V; ++c)
+    for (int v = 0; v < NV; ++v) {
+      S t[K];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) W[c][v] = Ops<A>::splat(a.bc_state[dir][v]);
+      for (int k = 0; k < K; ++k) t[k] = (S)a.bc_state[dir][v];
+#pragma unroll
+      for (int c = 0; c < V; ++c) W[c][v] = Ops<A>::pack(t);
+    }
     return;
   }
   const S *row = base + (long long)sj * a.pitch;
@@ -925,11 +933,28 @@ static __device__ __forceinline__ void lring_read(const LaneRing<typename Ops<A>
                                                   int r, A (&W)[V][NV]) {
   constexpr int K = Ops<A>::K;
   const int slot = r % D;
+  if constexpr (std::is_same<A, BF>::value && V % 2 == 0) {
+    // bfloat16 cells two at a time from the slot's 32-bit words: a bfloat16
+    // is the upper half of an FP32, so the cell in the low half (the lower
+    // address) widens to the word shifted up by 16, the one in the high half
+    // to the word with its low 16 bits cleared -- one bit operation per cell
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const typename Ops<A>::S *p = rg.slot(slot, v);
+    for (int v = 0; v < NV; ++v) {
+      const unsigned *q = reinterpret_cast<const unsigned *>(rg.slot(slot, v));
 #pragma unroll
-    for (int c = 0; c < V; ++c) W[c][v] = Ops<A>::pack(p + c * K);
+      for (int c = 0; c < V; c += 2) {
+        const unsigned w = q[c / 2];
+        W[c][v].v = __uint_as_float(w << 16);
+        W[c + 1][v].v = __uint_as_float(w & 0xffff0000u);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const typename Ops<A>::S *p = rg.slot(slot, v);
+#pragma unroll
+      for (int c = 0; c < V; ++c) W[c][v] = Ops<A>::pack(p + c * K);
+    }
   }
 }
 

@@ -19,7 +19,8 @@ namespace fv {
 #define FV_VARIANT_TB(R, PREC, V, TY, NW, MB, D, DESC)                                              \
   out.push_back(Variant{kAdvection, PREC, V, TY, NW, MB, D, async_smem_bytes<R, V, 1, -(D)>(NW),        \
                         reinterpret_cast<const void *>(&fv_step_kernel_tb<Advection, R, V, TY, NW, MB, D>), \
-                        DESC, 0, 2})
+                        DESC, 0, 2, 0,                                                                  \
+                        reinterpret_cast<const void *>(&fv_step_kernel_tb<Advection, R, V, TY, NW, MB, D, true>)})
 
 void register_step_advection(std::vector<Variant> &out) {
   FV_VARIANT_TB(double, 0, 2, 32, 4, 2, -4, "advection f64 v2 ty32 w4 b2 async4 tb2");

@@ -8,7 +8,6 @@
 // in four more state planes from the step that computes them to the next.
 #include "fv_internal.h"
 #include "fv_step.cuh"
-#include "fv_tb.cuh"
 
 namespace fv {
 
@@ -40,24 +39,8 @@ namespace fv {
                         reinterpret_cast<const void *>(&fv_step_kernel<Euler, A, V, TY, NW, true, MB, D, true>), \
                         DESC, 1})
 
-// Two-step kernels (fixed dt, periodic grids; see fv_tb.cuh).
-#define FV_VARIANT_TB(A, PREC, V, TY, NW, MB, D, DESC)                                                \
-  out.push_back(Variant{kEuler, PREC, (V) * Ops<A>::K, TY, NW, MB, D,                                   \
-                        async_smem_bytes<A, V, 4, (D < 0 ? -D : 1)>(NW),                                \
-                        reinterpret_cast<const void *>(&fv_step_kernel_tb<Euler, A, V, TY, NW, MB, D>), \
-                        DESC, 0, 2})
-
 void register_step_euler(std::vector<Variant> &out) {
-  FV_VARIANT_TB(float, 1, 2, 64, 4, 3, -4, "euler f32 v2 ty64 w4 b3 async4 tb2");
-  FV_VARIANT_TB(float, 1, 2, 128, 4, 3, -4, "euler f32 v2 ty128 w4 b3 async4 tb2");
-  FV_VARIANT_TB(float, 1, 2, 32, 4, 3, -4, "euler f32 v2 ty32 w4 b3 async4 tb2");
-  FV_VARIANT_TB(float, 1, 2, 64, 4, 3, -3, "euler f32 v2 ty64 w4 b3 async3 tb2");
-  FV_VARIANT_TB(float, 1, 2, 64, 4, 2, -4, "euler f32 v2 ty64 w4 b2 async4 tb2");
-  FV_VARIANT_TB(float, 1, 2, 16, 4, 3, -4, "euler f32 v2 ty16 w4 b3 async4 tb2");
-  FV_VARIANT_TB(double, 0, 2, 16, 4, 1, -4, "euler f64 v2 ty16 w4 b1 async4 tb2");
-  FV_VARIANT_TB(BF, 2, 2, 64, 4, 3, -4, "euler bf16 v2 ty64 w4 b3 async4 tb2");
-  FV_VARIANT_TB(BF, 2, 2, 32, 4, 2, -4, "euler bf16 v2 ty32 w4 b2 async4 tb2");
-  FV_VARIANT_TB(BF, 2, 2, 16, 4, 3, -4, "euler bf16 v2 ty16 w4 b3 async4 tb2");
+  register_step_euler_tb(out);  // two-step kernels first (fv_step_euler_tb.cu)
   FV_VARIANT_INPL_PC(0, 1, 64, 4, 3, -4, "euler f64 v1 ty64 w4 b3 async4 inplace pc");
   FV_VARIANT_INPL_PC(0, 1, 16, 4, 3, -4, "euler f64 v1 ty16 w4 b3 async4 inplace pc");
   FV_VARIANT_INPL(float, 1, 4, 32, 4, 3, -4, "euler f32 v4 ty32 w4 b3 async4 inplace");

@@ -1,5 +1,5 @@
 // fv_tb.cuh -- two time steps per pass over the state (temporal blocking),
-// for the paper's constant dt (Sec. 2.2.1) on a grid periodic in x and y.
+// for the paper's constant dt (Sec. 2.2.1), with any boundary conditions.
 //
 // One warp task marches up its strip as in fv_step.cuh, but each row of W^n
 // it loads feeds two levels of the march: level 1 turns W^n rows into W^{n+1}
@@ -9,8 +9,15 @@
 // y0 - 2 .. y1 + 1, and each lane holds V >= 2 cells, so the halo lanes 0
 // and 31 carry the two halo columns a double step needs; level 1 computes
 // W^{n+1} on the one-cell ring around the task (its other halo values are
-// never used).  Ghost cells of a periodic grid are cells of the grid, so
-// wrapping rows and columns is all the boundary handling there is.
+// never used).  Ghost cells of a periodic side are cells of the grid, so
+// there rows and columns simply wrap.  On a transmissive or Dirichlet side
+// the ring cells beyond the boundary are ghosts of W^{n+1}, not cells of
+// the scheme: level 1 loads the ghosts of W^n from the boundary condition
+// (a second ghost layer, which only feeds ring cells that are replaced, is
+// a copy of the first), and before level 2 reads a level-1 row, its ghost
+// cells are replaced by the boundary condition applied to W^{n+1} (a copy
+// of the border cell as stored, or the prescribed state), exactly what the
+// single step's loader would give them.
 //
 // Level 1 and level 2 use exactly the arithmetic of a single step, so a pass
 // gives the bits of two single steps.  The paper's check dt lmax(W^{n+1}) <=
@@ -31,32 +38,142 @@ static __device__ __forceinline__ int tb_wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-// Copies of W^n row j (any integer: wrapped) into ring slot r % D; each
-// lane's N cells, wrapped in x.
-template <class A, int V, int NV, int D, class G>
+// Source of index i (a row or a column, any integer) of W^n along an axis of
+// n cells whose low and high sides have boundary conditions blo and bhi: the
+// wrapped index on a periodic axis; else the index itself inside the grid
+// and, beyond it, the border cell (transmissive) or, through *dir, the
+// Dirichlet side (sides slo and shi).  Only the first ghost layer feeds
+// cells the pass keeps; the second one just has to be finite.
+static __device__ __forceinline__ int tb_src(int i, int n, int blo, int bhi, int slo, int shi, int &dir) {
+  dir = -1;
+  if (i < 0) {
+    if (blo == kPeriodic) return tb_wrap(i, n);
+    if (blo == kDirichlet) dir = slo;
+    return 0;
+  }
+  if (i >= n) {
+    if (bhi == kPeriodic) return tb_wrap(i, n);
+    if (bhi == kDirichlet) dir = shi;
+    return n - 1;
+  }
+  return i;
+}
+
+// Copies of W^n row j (any integer) into ring slot r % D: each lane's N
+// cells, wrapped when every side is periodic (NP false), else through
+// tb_src in both directions, Dirichlet ghost cells being stored directly in
+// the storage type, as the single step's ring does.
+template <class A, int V, int NV, int D, bool NP, class G>
 static __device__ __forceinline__ void tb_issue(const G &a, const typename Ops<A>::S *src, int X, bool xin,
                                                 const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
                                                 int r, int j) {
   using S = typename Ops<A>::S;
   constexpr int N = V * Ops<A>::K;
   const int slot = r % D;
-  const S *g = src + (long long)tb_wrap(j, a.ny) * a.pitch;
-  if (xin) {
+  if constexpr (!NP) {
+    // every side periodic: rows and columns wrap
+    const S *g = src + (long long)tb_wrap(j, a.ny) * a.pitch;
+    if (xin) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), g + X + v * a.plane);
+    } else {
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        const int col = tb_wrap(X + c, a.nx);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          S *d = rg.slot(slot, v) + c;
+          if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, g + col + v * a.plane);
+          else *d = __ldcg(g + col + v * a.plane);
+        }
+      }
+    }
+    cp_async_commit();
+    return;
+  }
+  int rdir;
+  const int sj = tb_src(j, a.ny, a.bc[kS], a.bc[kN], kS, kN, rdir);
+  const S *g = src + (long long)sj * a.pitch;
+  if (rdir >= 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = (S)a.bc_state[rdir][v];
+  } else if (xin) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), g + X + v * a.plane);
   } else {
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-      const int col = tb_wrap(X + c, a.nx);
+      int cdir;
+      const int col = tb_src(X + c, a.nx, a.bc[kW], a.bc[kE], kW, kE, cdir);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         S *d = rg.slot(slot, v) + c;
-        if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, g + col + v * a.plane);
+        if (cdir >= 0) *d = (S)a.bc_state[cdir][v];
+        else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, g + col + v * a.plane);
         else *d = __ldcg(g + col + v * a.plane);
       }
     }
   }
   cp_async_commit();
+}
+
+// The prescribed state of side `side` as a stored cell (rounded to the
+// storage type), in every cell of a row of the lane.
+template <class A, int V, int NV, class G>
+static __device__ __forceinline__ void tb_dirichlet_row(const G &a, int side, A (&W)[V][NV]) {
+  using S = typename Ops<A>::S;
+  constexpr int K = Ops<A>::K;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    S t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = (S)a.bc_state[side][v];
+#pragma unroll
+    for (int c = 0; c < V; ++c) W[c][v] = Ops<A>::pack(t);
+  }
+}
+
+// Ghost columns of a level-1 row (W^{n+1}, rounded to storage) on the
+// non-periodic sides: column -1 (lane 0's last cell on the first strip) and
+// column nx (in the lane whose cells reach past the grid on the last strip)
+// take the boundary condition applied to W^{n+1}.  Every lane takes part in
+// the shuffles.  X0: the strip's first column.
+template <class A, int V, int NV, class G>
+static __device__ __forceinline__ void tb_fix_cols(const G &a, A (&W)[V][NV], int X, int X0, int lane) {
+  static_assert(Ops<A>::K == 1, "two-step passes use one cell per value");
+  using O = Ops<A>;
+  using S = typename O::S;
+  constexpr int N = V;
+  if (a.bc[kW] != kPeriodic && X0 == 0) {
+    A g[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const A w0 = O::shfl_down(W[0][v], 1);  // lane 1's first cell: column 0
+      S t[1] = {(S)a.bc_state[kW][v]};
+      g[v] = a.bc[kW] == kDirichlet ? O::pack(t) : w0;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) W[V - 1][v] = g[v];
+    }
+  }
+  if (a.bc[kE] != kPeriodic && X0 + 30 * N >= a.nx) {
+    A up[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) up[v] = O::shfl_up(W[V - 1][v], 1);  // the west lane's last cell
+    const int rel = a.nx - X;  // this lane's cell holding column nx, if 0 <= rel < N
+#pragma unroll
+    for (int c = 0; c < V; ++c)
+      if (c == rel) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          S t[1] = {(S)a.bc_state[kE][v]};
+          W[c][v] = a.bc[kE] == kDirichlet ? O::pack(t) : (c == 0 ? up[v] : W[c > 0 ? c - 1 : 0][v]);
+        }
+      }
+  }
 }
 
 // One row of one level: x-work of `nxt`, the y-face between `cur` and `nxt`,
@@ -142,20 +259,24 @@ static __device__ __forceinline__ void tb_store(const G &a, const A (&Wn)[V][Sys
 }
 
 // The two-level march of one warp task (rows [y0, y1) of W^{n+2}).
-template <class Sys, class A, int V, int D, class G>
+template <class Sys, class A, int V, int D, bool NP, class G>
 static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &P, const typename Ops<A>::S *src,
                                                 typename Ops<A>::S *dst,
                                                 const LaneRing<typename Ops<A>::S, V * Ops<A>::K, Sys::NV, D> &rg,
-                                                int X, bool xin, int y0, int y1, bool writer, A lx, A ly,
-                                                typename Ops<A>::P &lam1, unsigned &bad1,
+                                                int X, int X0, int lane, bool xin, int y0, int y1, bool writer,
+                                                A lx, A ly, typename Ops<A>::P &lam1, unsigned &bad1,
                                                 typename Ops<A>::P &lam2, unsigned &bad2) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV;
   using O = Ops<A>;
   S *dst_lane = dst + X;
+  // ghost rows of W^{n+1} below row 0 and above row ny - 1 on non-periodic
+  // sides (NP: the kernel built for grids with such sides)
+  const bool gS = NP && a.bc[kS] != kPeriodic && y0 == 0;
+  const bool gN = NP && a.bc[kN] != kPeriodic && y1 == a.ny;
   const int nrows = y1 - y0 + 4;  // W^n rows y0 - 2 .. y1 + 1
   auto issue = [&](int r) {
-    if (r < nrows) tb_issue<A, V, NV, D>(a, src, X, xin, rg, r, y0 - 2 + r);
+    if (r < nrows) tb_issue<A, V, NV, D, NP>(a, src, X, xin, rg, r, y0 - 2 + r);
     else cp_async_commit();
   };
   auto fetch = [&](int r, A(&W)[V][NV]) {
@@ -186,22 +307,37 @@ static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &
   fetch(2, R1a.W);
   tb_level_row<Sys, A, V>(P, R1b, R1a, Fs1, lx, ly, Wn);
   tb_round_to_storage<A, V, NV>(Wn);
+  if constexpr (NP) tb_fix_cols<A, V, NV>(a, Wn, X, X0, lane);
 #pragma unroll
-  for (int c = 0; c < V; ++c) {
+  for (int c = 0; c < V; ++c)
 #pragma unroll
     for (int v = 0; v < NV; ++v) R2a.W[c][v] = Wn[c][v];
-    A Fx_[NV], sx_;
-    Sys::fluxes(R2a.W[c], P, Fx_, sx_, R2a.Fy[c], R2a.sy[c]);
-  }
   // W^{n+1} row y0: level 2's first own row
   fetch(3, R1b.W);
   tb_level_row<Sys, A, V>(P, R1a, R1b, Fs1, lx, ly, Wn);
   tb_lambda<Sys, A, V>(P, Wn, X, a.nx, writer, lam1, bad1);
   tb_round_to_storage<A, V, NV>(Wn);
+  if constexpr (NP) tb_fix_cols<A, V, NV>(a, Wn, X, X0, lane);
 #pragma unroll
   for (int c = 0; c < V; ++c)
 #pragma unroll
     for (int v = 0; v < NV; ++v) R2b.W[c][v] = Wn[c][v];
+  // below row 0 of a non-periodic grid the halo row is the ghost of W^{n+1}
+  if (gS) {
+    if (a.bc[kS] == kDirichlet) {
+      tb_dirichlet_row<A, V, NV>(a, kS, R2a.W);
+    } else {
+#pragma unroll
+      for (int c = 0; c < V; ++c)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) R2a.W[c][v] = R2b.W[c][v];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    A Fx_[NV], sx_;
+    Sys::fluxes(R2a.W[c], P, Fx_, sx_, R2a.Fy[c], R2a.sy[c]);
+  }
   row_x<Sys, V>(P, R2b.W, R2b.Fy, R2b.sy, R2b.dX);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
@@ -218,10 +354,22 @@ static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &
     tb_level_row<Sys, A, V>(P, R1b, R1a, Fs1, lx, ly, Wn);
     if (k < y1) tb_lambda<Sys, A, V>(P, Wn, X, a.nx, writer, lam1, bad1);
     tb_round_to_storage<A, V, NV>(Wn);
+    if constexpr (NP) tb_fix_cols<A, V, NV>(a, Wn, X, X0, lane);
 #pragma unroll
     for (int c = 0; c < V; ++c)
 #pragma unroll
       for (int v = 0; v < NV; ++v) R2a.W[c][v] = Wn[c][v];
+    if (gN && k == y1) {
+      // row ny: the ghost of W^{n+1} above the grid (R2b holds row ny - 1)
+      if (a.bc[kN] == kDirichlet) {
+        tb_dirichlet_row<A, V, NV>(a, kN, R2a.W);
+      } else {
+#pragma unroll
+        for (int c = 0; c < V; ++c)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) R2a.W[c][v] = R2b.W[c][v];
+      }
+    }
     tb_level_row<Sys, A, V>(P, R2b, R2a, Fs2, lx, ly, Wm);
     tb_store<Sys, A, V>(a, Wm, dst_lane, X, k - 1, writer);
     tb_lambda<Sys, A, V>(P, Wm, X, a.nx, writer, lam2, bad2);
@@ -231,10 +379,21 @@ static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &
     tb_level_row<Sys, A, V>(P, R1a, R1b, Fs1, lx, ly, Wn);
     if (k < y1) tb_lambda<Sys, A, V>(P, Wn, X, a.nx, writer, lam1, bad1);
     tb_round_to_storage<A, V, NV>(Wn);
+    if constexpr (NP) tb_fix_cols<A, V, NV>(a, Wn, X, X0, lane);
 #pragma unroll
     for (int c = 0; c < V; ++c)
 #pragma unroll
       for (int v = 0; v < NV; ++v) R2b.W[c][v] = Wn[c][v];
+    if (gN && k == y1) {
+      if (a.bc[kN] == kDirichlet) {
+        tb_dirichlet_row<A, V, NV>(a, kN, R2b.W);
+      } else {
+#pragma unroll
+        for (int c = 0; c < V; ++c)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) R2b.W[c][v] = R2a.W[c][v];
+      }
+    }
     tb_level_row<Sys, A, V>(P, R2a, R2b, Fs2, lx, ly, Wm);
     tb_store<Sys, A, V>(a, Wm, dst_lane, X, k - 1, writer);
     tb_lambda<Sys, A, V>(P, Wm, X, a.nx, writer, lam2, bad2);
@@ -313,8 +472,10 @@ static __device__ __forceinline__ void finish_tb(Ctrl *ctrl, const StepStart &st
   }
 }
 
-// The two-step kernel (cp.async ring staging only, D < 0).
-template <class Sys, class A, int V, int TY, int NW, int MINB, int D>
+// The two-step kernel (cp.async ring staging only, D < 0).  NP: built for
+// grids with a transmissive or Dirichlet side (the ghost handling costs
+// registers, so grids periodic on every side run the kernel without it).
+template <class Sys, class A, int V, int TY, int NW, int MINB, int D, bool NP = false>
 __global__ void __launch_bounds__(NW * 32, MINB)
 fv_step_kernel_tb(const StepArgs<typename Ops<A>::S> a) {
   static_assert(D < 0 && V * Ops<A>::K >= 2, "two-step passes need the cp.async ring and two halo cells per lane");
@@ -345,11 +506,13 @@ fv_step_kernel_tb(const StepArgs<typename Ops<A>::S> a) {
     for (int task = gw; task < a.ntasks; task += GW) {
       const int sx_ = task % a.nstrips;
       const int cy = task / a.nstrips;
-      const int X = sx_ * (30 * N) + (lane - 1) * N;
+      const int X0 = sx_ * (30 * N);
+      const int X = X0 + (lane - 1) * N;
       const int y0 = cy * TY;
       const int y1 = min(y0 + TY, a.ny);
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
-      march_tb<Sys, A, V, DA>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam1, bad1, lam2, bad2);
+      march_tb<Sys, A, V, DA, NP>(a, P, src, dst, lrg, X, X0, lane, xin, y0, y1, writer, lx, ly, lam1, bad1,
+                                  lam2, bad2);
     }
   }
   finish_tb<NW>(a.ctrl, st, a.pol, (double)lam1, bad1 != 0u, (double)lam2, bad2 != 0u, s_lam, s_bad);
