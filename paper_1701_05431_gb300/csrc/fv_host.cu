@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -353,6 +354,7 @@ static StepArgs<R> make_args(const fv_ctx *c, const Variant &V) {
     a.ovl[0] = (R *)c->ovl;
     a.ovl[1] = (R *)((char *)c->ovl + c->ovl_parity_bytes);
     a.ovl_task = c->ovl_task;
+    a.ovl_bc = (const R *)((char *)c->ovl + 2 * c->ovl_parity_bytes);
   }
   a.ctrl = c->ctrl;
   a.nx = c->cfg.nx;
@@ -677,29 +679,52 @@ static fv_status ensure_staging(fv_ctx *c, size_t bytes) {
 // Recompute lmax of the current state into slot `step % 3`, clear the other
 // slots and report an inadmissible state.
 // In-place mode: overlap strips of parity step % 2 from the state.
+// The overlap strips of both parities from the state (the step reads those
+// of parity step % 2; filling the other parity too leaves no strip cell
+// unset, also the ones a ragged last strip never rewrites), and the four
+// sides' prescribed states as stored cells after them.
 static fv_status fill_ovl(fv_ctx *c, long long step) {
+  (void)step;
   const Variant &V = all_variants()[c->variant];
   const int sw = 30 * V.V;
   const int nstrips = (c->cfg.nx + sw - 1) / sw, nchunks = (c->cfg.ny + V.TY - 1) / V.TY;
-  void *dst = (char *)c->ovl + ((step & 1) ? c->ovl_parity_bytes : 0);
   // kernels that carry the primitives keep them in the strips too
   const int nv = V.carry ? c->nplanes : c->nvar;
-  const long long total = (long long)nstrips * nchunks * nv * (2 * V.TY + 2 * sw);
+  const long long total = (long long)nstrips * nchunks * nv * (2 * V.TY * V.V + 2 * sw);
   const int th = 256;
   const int g = (int)std::min<long long>((total + th - 1) / th, 4LL * c->sms * 8);
   const int p = c->cfg.precision;
-  if (p == 0)
-    fill_ovl_kernel<double><<<g, th, 0, c->stream>>>((const double *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
-                                                     c->plane, nv, nstrips, nchunks, V.TY, sw, c->ovl_task,
-                                                     (double *)dst);
-  else if (p == 1)
-    fill_ovl_kernel<float><<<g, th, 0, c->stream>>>((const float *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
-                                                    c->plane, nv, nstrips, nchunks, V.TY, sw, c->ovl_task,
-                                                    (float *)dst);
-  else
-    fill_ovl_kernel<__nv_bfloat16><<<g, th, 0, c->stream>>>((const __nv_bfloat16 *)c->buf[0], c->cfg.nx, c->cfg.ny,
-                                                            c->pitch, c->plane, nv, nstrips, nchunks, V.TY,
-                                                            sw, c->ovl_task, (__nv_bfloat16 *)dst);
+  for (int parity = 0; parity < 2; ++parity) {
+    void *dst = (char *)c->ovl + (parity ? c->ovl_parity_bytes : 0);
+    if (p == 0)
+      fill_ovl_kernel<double><<<g, th, 0, c->stream>>>((const double *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
+                                                       c->plane, nv, nstrips, nchunks, V.TY, V.V, sw, c->ovl_task,
+                                                       (double *)dst);
+    else if (p == 1)
+      fill_ovl_kernel<float><<<g, th, 0, c->stream>>>((const float *)c->buf[0], c->cfg.nx, c->cfg.ny, c->pitch,
+                                                      c->plane, nv, nstrips, nchunks, V.TY, V.V, sw, c->ovl_task,
+                                                      (float *)dst);
+    else
+      fill_ovl_kernel<__nv_bfloat16><<<g, th, 0, c->stream>>>((const __nv_bfloat16 *)c->buf[0], c->cfg.nx,
+                                                              c->cfg.ny, c->pitch, c->plane, nv, nstrips, nchunks,
+                                                              V.TY, V.V, sw, c->ovl_task, (__nv_bfloat16 *)dst);
+    FV_CUDA(c, cudaGetLastError());
+  }
+  // slots 4..7 of a Dirichlet state: its carried primitives, as make_args passes them
+  void *bc = (char *)c->ovl + 2 * c->ovl_parity_bytes;
+  auto bc_cells = [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    BcCells<S> b;
+    for (int s2 = 0; s2 < 4; ++s2) {
+      for (int v = 0; v < 8; ++v) b.v[s2][v] = (typename ParamOf<S>::T)c->cfg.bc_state[s2][v];
+      if (V.carry)
+        for (int v = 0; v < 4; ++v) b.v[s2][4 + v] = (typename ParamOf<S>::T)c->bc_pc[s2][v];
+    }
+    fill_bc_cells_kernel<S><<<1, 128, 0, c->stream>>>(b, nv, V.V, (S *)bc);
+  };
+  if (p == 0) bc_cells((double *)nullptr);
+  else if (p == 1) bc_cells((float *)nullptr);
+  else bc_cells((__nv_bfloat16 *)nullptr);
   FV_CUDA(c, cudaGetLastError());
   FV_CUDA(c, cudaStreamSynchronize(c->stream));
   return FV_OK;
@@ -1222,10 +1247,12 @@ extern "C" fv_status fv_set_inplace(fv_ctx *c, int on) {
     const long long ntasks = (long long)((c->cfg.nx + sw - 1) / sw) * ((c->cfg.ny + V.TY - 1) / V.TY);
     const int q = (int)(16 / c->esize);  // keep every task's strips 16-byte aligned
     const int nv = V.carry ? c->nplanes : c->nvar;  // strips hold the carried planes too
-    const int ts = (nv * (2 * V.TY + 2 * sw) + q - 1) / q * q;
+    const int ts = (nv * (2 * V.TY * V.V + 2 * sw) + q - 1) / q * q;
     const size_t pb = ((size_t)ntasks * ts * c->esize + 255) / 256 * 256;
     void *ovl = nullptr;
-    cudaError_t e = cudaMalloc(&ovl, 2 * pb);
+    // two parities of strips, then the sides' prescribed states as cells
+    // (4 sides x up to 8 variables x 4 cells of up to 8 bytes)
+    cudaError_t e = cudaMalloc(&ovl, 2 * pb + 1024);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(overlap strips)");
     if (c->has_state && c->h_ctrl->cur == 1u) {
       // the state goes to buffer 0, which becomes the only one

@@ -54,6 +54,7 @@ template <class S> struct StepArgs {
   // default ping-pong mode, where buf0 != buf1)
   S *ovl[2];
   int ovl_task;      // elements of one task's strips in one parity
+  const S *ovl_bc;   // the four sides' prescribed states as stored cells, [side][variable][cells per lane]
 };
 
 // What the march reads of the launch arguments.  The single-instance kernel
@@ -290,12 +291,14 @@ static __device__ __forceinline__ void row_x(const SysParams<A> &P, const A (&W)
 // place; the cells of its halo that belong to other tasks are read from the
 // overlap strips those tasks wrote one step earlier (the paper's ovlpE/N/W/S
 // buffers, Sec. 4.1.2, filled by the producing task instead of a copy task):
-// per task and step parity, its west and east border columns (TY values each)
-// and its south and north border rows (30 N values each), for every
-// variable.  Step n reads the strips of parity n % 2 and writes those of
-// parity (n + 1) % 2, so no task reads a value another task is overwriting.
-// A task's own rows are read (through the ring, several rows ahead) before it
-// overwrites them.
+// per task and step parity, for every variable, its first and last N
+// columns (the west and east column strips, TY rows of N cells: exactly the
+// cells the halo lane of the neighbouring task holds, so that lane reads one
+// vector per row like every other lane) and its first and last rows (the
+// south and north row strips, 30 N cells).  Step n reads the strips of
+// parity n % 2 and writes those of parity (n + 1) % 2, so no task reads a
+// value another task is overwriting.  A task's own rows are read (through
+// the ring, several rows ahead) before it overwrites them.
 template <class S> struct Ovl {
   const S *rd;     // strips of parity n % 2 (borders of W^n)
   S *wr;           // strips of parity (n + 1) % 2 (borders of W^{n+1})
@@ -304,137 +307,167 @@ template <class S> struct Ovl {
   int X0, y0, y1;  // first column, first and end row of the task
   int ty, ts;      // rows per task, elements per task in one parity
   // per lane, set once per task by ovl_lane_setup
-  const S *hp;     // halo lanes: source of their used cell in row y0
-  long long hvs;   // its variable stride
-  int hkind, hdir; // 0 state / 2 column strip, Dirichlet side (-1: none)
+  const S *op;     // own rows: source of row y0 (the state, or a neighbour's column strip)
+  int ors;         // its row stride
+  long long ovs;   // its variable stride
   S *wb;           // this task's strips of parity (n + 1) % 2
-  int ecell;       // the lane's cell that is the task's last real column (-1: none)
+  const S *dstrip; // the prescribed states of the four sides as stored cells: [side][variable][N cells]
+  unsigned flags;  // kPercell | fixW (bits 1-2) | fixE (bits 3-4) | kLastFull
 };
+enum : unsigned { kPercell = 1u, kFixWShift = 1, kFixEShift = 3, kLastFull = 32u };
 
 // Element offsets inside one task's strips (NV variables each).
-template <int NV, int SW> struct OvlLayout {
+template <int NV, int N, int SW> struct OvlLayout {
   static __device__ __forceinline__ int colW(int ty) { return 0; }
-  static __device__ __forceinline__ int colE(int ty) { return NV * ty; }
-  static __device__ __forceinline__ int rowS(int ty) { return 2 * NV * ty; }
-  static __device__ __forceinline__ int rowN(int ty) { return 2 * NV * ty + NV * SW; }
+  static __device__ __forceinline__ int colE(int ty) { return NV * ty * N; }
+  static __device__ __forceinline__ int rowS(int ty) { return 2 * NV * ty * N; }
+  static __device__ __forceinline__ int rowN(int ty) { return 2 * NV * ty * N + NV * SW; }
 };
 
-// Where cell (j, col) of a task's halo-extended tile comes from in place:
-// a Dirichlet side (dir >= 0), or an address p of variable 0 with variable
-// stride vs (the state itself for the task's own cells and for transmissive
-// ghosts, which copy the task's own border, else a neighbour's strip).
-// Cells no face of the task uses (tile corners, idle cells of the halo
-// lanes) resolve to some valid finite value.
-template <int NV, int SW, class G, class S>
-static __device__ __forceinline__ const S *inplace_cell(const G &a, const S *W, const Ovl<S> &o, int j, int col,
-                                                        long long &vs, int &dir, int &kind) {
-  using L = OvlLayout<NV, SW>;
-  dir = -1;
-  kind = 1;  // a row strip, unless changed below
-  const int last = min(o.X0 + SW, a.nx) - 1;  // last real column of the task
-  const int cc = min(max(col, o.X0), last) - o.X0;
-  if (j < o.y0) {
-    if (j < 0) {
-      if (a.bc[kS] == kDirichlet) { dir = kS; return nullptr; }
-      if (a.bc[kS] == kPeriodic) {
-        vs = SW;
-        return o.rd + (long long)((o.nchunks - 1) * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + cc;
-      }
-      j = 0;  // transmissive: the task's own first row
-    } else {
-      vs = SW;
-      return o.rd + (long long)((o.cy - 1) * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + cc;
-    }
-  } else if (j >= o.y1) {
-    if (j >= a.ny) {
-      if (a.bc[kN] == kDirichlet) { dir = kN; return nullptr; }
-      if (a.bc[kN] == kPeriodic) {
-        vs = SW;
-        return o.rd + (long long)o.sx * o.ts + L::rowS(o.ty) + cc;
-      }
-      j = a.ny - 1;  // transmissive: the task's own last row
-    } else {
-      vs = SW;
-      return o.rd + (long long)((o.cy + 1) * o.nstrips + o.sx) * o.ts + L::rowS(o.ty) + cc;
-    }
-  }
-  const int jr = j - o.y0;
-  kind = 2;  // a column strip, unless the cell is the state's
-  if (col < o.X0) {
-    if (o.X0 == 0) {
-      if (a.bc[kW] == kDirichlet) { dir = kW; return nullptr; }
-      if (a.bc[kW] == kPeriodic) {
-        vs = o.ty;
-        return o.rd + (long long)(o.cy * o.nstrips + o.nstrips - 1) * o.ts + L::colE(o.ty) + jr;
-      }
-      col = 0;  // transmissive: the task's own first column
-    } else {
-      vs = o.ty;
-      return o.rd + (long long)(o.cy * o.nstrips + o.sx - 1) * o.ts + L::colE(o.ty) + jr;
-    }
-  } else if (col > last) {
-    if (last == a.nx - 1) {
-      if (a.bc[kE] == kDirichlet) { dir = kE; return nullptr; }
-      if (a.bc[kE] == kPeriodic) {
-        vs = o.ty;
-        return o.rd + (long long)(o.cy * o.nstrips) * o.ts + L::colW(o.ty) + jr;
-      }
-      col = a.nx - 1;  // transmissive: the task's own last column
-    } else {
-      vs = o.ty;
-      return o.rd + (long long)(o.cy * o.nstrips + o.sx + 1) * o.ts + L::colW(o.ty) + jr;
-    }
-  }
-  kind = 0;
-  vs = a.plane;
-  return W + (long long)j * a.pitch + col;
-}
-
-// Per-lane in-place bookkeeping of one task: where a halo lane's used cell
-// comes from in the task's first row (later rows follow at stride 1 in a
-// column strip or `pitch` in the state), the task's own output strips and
-// the lane's cell holding the task's last real column.
+// Per-lane in-place bookkeeping of one task: where the lane's N cells of the
+// task's own rows come from, whether a ghost column has to be set after a
+// read, and where the task's strips of the next parity go.  Lanes 1..30 read
+// their own cells from the state; the halo lanes read the neighbouring
+// task's column strip (periodic sides: the task across the boundary), on a
+// Dirichlet side the prescribed state's cells, and on a transmissive side
+// some of their own task's cells, the ghost being set in registers
+// (ovl_fix_cols).  Lanes of a ragged last strip that reach past the grid go
+// cell by cell.
 template <int NV, int N, class G, class S>
 static __device__ __forceinline__ void ovl_lane_setup(const G &a, const S *W, Ovl<S> &o, int X, int lane) {
   constexpr int SW = 30 * N;
-  o.hp = nullptr;
-  o.hvs = 0;
-  o.hkind = 0;
-  o.hdir = -1;
-  if (lane == 0 || lane == 31)
-    o.hp = inplace_cell<NV, SW>(a, W, o, o.y0, X + (lane == 0 ? N - 1 : 0), o.hvs, o.hdir, o.hkind);
+  using L = OvlLayout<NV, N, SW>;
+  const bool full = o.X0 + SW <= a.nx;  // every column of the strip lies in the grid
+  unsigned f = (lane >= 1 && X + N > a.nx) ? kPercell : 0u;
+  o.op = W + (long long)o.y0 * a.pitch + X;
+  o.ors = (int)a.pitch;
+  o.ovs = a.plane;
+  if (lane == 0) {
+    if (o.sx > 0 || a.bc[kW] == kPeriodic) {
+      o.op = o.rd + (long long)(o.cy * o.nstrips + (o.sx > 0 ? o.sx - 1 : o.nstrips - 1)) * o.ts + L::colE(o.ty);
+      o.ors = N;
+      o.ovs = (long long)o.ty * N;
+    } else if (a.bc[kW] == kDirichlet) {
+      o.op = o.dstrip + kW * NV * N;  // the same N cells every row
+      o.ors = 0;
+      o.ovs = N;
+    } else {
+      o.op = W + (long long)o.y0 * a.pitch + o.X0;
+    }
+  } else if (lane == 31 && !(f & kPercell)) {
+    if (o.sx < o.nstrips - 1 || a.bc[kE] == kPeriodic) {
+      o.op = o.rd + (long long)(o.cy * o.nstrips + (o.sx < o.nstrips - 1 ? o.sx + 1 : 0)) * o.ts + L::colW(o.ty);
+      o.ors = N;
+      o.ovs = (long long)o.ty * N;
+    } else if (a.bc[kE] == kDirichlet) {
+      o.op = o.dstrip + kE * NV * N;
+      o.ors = 0;
+      o.ovs = N;
+    } else {
+      o.op = W + (long long)o.y0 * a.pitch + (X - N);
+    }
+  }
+  // transmissive west or east side: the halo lane's ghost cell is a copy of the border column
+  if (o.sx == 0 && a.bc[kW] == kTransmissive) f |= 1u << kFixWShift;
+  if (full && o.sx == o.nstrips - 1 && a.bc[kE] == kTransmissive) f |= 1u << kFixEShift;
+  if (full) f |= kLastFull;
+  o.flags = f;
   o.wb = o.wr + (long long)(o.cy * o.nstrips + o.sx) * o.ts;
-  const int last = min(o.X0 + SW, a.nx) - 1;
-  o.ecell = (last >= X && last < X + N) ? last - X : -1;
+}
+
+// Source of a lane's N cells of halo row j (j = y0 - 1 or y1), always a
+// vector inside the strips: the row strip of the task below or above
+// (across a periodic side: the task at the other end), for a transmissive
+// ghost row the task's own border row strip (its border row of W^n), or the
+// prescribed state's cells.  The halo lanes' cells there are tile corners no
+// face uses: they read the strip at lane 1's or lane 30's position, and so
+// do the lanes of a ragged last strip past the grid.
+template <int NV, int N, class G, class S>
+static __device__ __forceinline__ const S *ovl_halo_src(const G &a, const S *W, const Ovl<S> &o, int X, int j,
+                                                        long long &vs) {
+  constexpr int SW = 30 * N;
+  using L = OvlLayout<NV, N, SW>;
+  const int xo = min(max(X - o.X0, 0), SW - N);
+  vs = SW;
+  if (j < o.y0) {
+    if (o.cy > 0 || a.bc[kS] == kPeriodic)
+      return o.rd + (long long)((o.cy > 0 ? o.cy - 1 : o.nchunks - 1) * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + xo;
+    if (a.bc[kS] == kDirichlet) {
+      vs = N;
+      return o.dstrip + kS * NV * N;
+    }
+    // transmissive: the task's own first row, as its south row strip holds it
+    return o.rd + (long long)(o.cy * o.nstrips + o.sx) * o.ts + L::rowS(o.ty) + xo;
+  }
+  if (o.cy < o.nchunks - 1 || a.bc[kN] == kPeriodic)
+    return o.rd + (long long)((o.cy < o.nchunks - 1 ? o.cy + 1 : 0) * o.nstrips + o.sx) * o.ts + L::rowS(o.ty) + xo;
+  if (a.bc[kN] == kDirichlet) {
+    vs = N;
+    return o.dstrip + kN * NV * N;
+  }
+  // transmissive: the task's own last row, as its north row strip holds it
+  return o.rd + (long long)(o.cy * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + xo;
+}
+
+// Ghost columns of a row just read, on a transmissive west or east side
+// (warp-uniform): lane 0's last cell becomes lane 1's first, lane 31's first
+// cell lane 30's last -- copies of the border columns, what the two-buffer
+// loader reads there.  (The ghost of a ragged last strip comes cell by cell.)
+template <class A, int V, int NV, class G, class S>
+static __device__ __forceinline__ void ovl_fix_cols(const G &a, const Ovl<S> &o, A (&W)[V][NV], int lane) {
+  using O = Ops<A>;
+  static_assert(O::K == 1, "in-place kernels hold one cell per value");
+  if (o.flags & (3u << kFixWShift)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const A w0 = O::shfl_down(W[0][v], 1);
+      if (lane == 0) W[V - 1][v] = w0;
+    }
+  }
+  if (o.flags & (3u << kFixEShift)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const A wl = O::shfl_up(W[V - 1][v], 1);
+      if (lane == 31) W[0][v] = wl;
+    }
+  }
 }
 
 // In-place mode: the writer lanes' share of the task's new border strips
-// (row y0 -> south row strip, row y1 - 1 -> north row strip, first and last
-// real column -> west and east column strips), values of W^{n+1} in storage
-// type, t[v][c] for the lane's N cells.
+// (row y0 -> south row strip, row y1 - 1 -> north row strip; lanes 1 and 30
+// -> the west and east column strips, N cells a row; on a ragged last strip
+// the lane holding the task's last column puts it in cell N - 1 of the east
+// column strip), values of W^{n+1} in storage type, t[v][c] for the lane's
+// N cells.
 template <int NV, int N, class G, class S>
 static __device__ __forceinline__ void write_strips(const G &a, const Ovl<S> &o, int X, int j, const S (&t)[NV][N]) {
   constexpr int SW = 30 * N;
-  using L = OvlLayout<NV, SW>;
-  if (j == o.y0) {
+  using L = OvlLayout<NV, N, SW>;
+  if (j == o.y0 || j == o.y1 - 1) {
+    // a one-row task writes its row to both row strips
+    const int first = j == o.y0 ? L::rowS(o.ty) : L::rowN(o.ty);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + L::rowS(o.ty) + v * SW + (X - o.X0), t[v]);
-  }
-  if (j == o.y1 - 1) {
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + first + v * SW + (X - o.X0), t[v]);
+    if (o.y1 - o.y0 == 1) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + L::rowN(o.ty) + v * SW + (X - o.X0), t[v]);
+      for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + L::rowN(o.ty) + v * SW + (X - o.X0), t[v]);
+    }
   }
   const int jr = j - o.y0;
-  if (X == o.X0) {
+  const int lane = threadIdx.x & 31;
+  const bool full = (o.flags & kLastFull) != 0u;
+  if (lane == 1 || (full && lane == 30)) {
+    S *cs = o.wb + (lane == 1 ? L::colW(o.ty) : L::colE(o.ty)) + jr * N;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) o.wb[L::colW(o.ty) + v * o.ty + jr] = t[v][0];
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(cs + (long long)v * o.ty * N, t[v]);
   }
-  if (o.ecell >= 0) {
+  if (!full) {
+    const int ecell = min(o.X0 + SW, a.nx) - 1 - X;  // the task's last column, if this lane holds it
 #pragma unroll
     for (int c = 0; c < N; ++c)
-      if (c == o.ecell) {
+      if (c == ecell) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) o.wb[L::colE(o.ty) + v * o.ty + jr] = t[v][c];
+        for (int v = 0; v < NV; ++v) o.wb[L::colE(o.ty) + v * o.ty * N + jr * N + (N - 1)] = t[v][c];
       }
   }
 }
@@ -851,79 +884,71 @@ static __device__ __forceinline__ void lring_issue(const G &a,
   cp_async_commit();
 }
 
-// In-place counterpart of lring_issue.  Lanes 1..30 with all N cells in the
-// grid copy one vector per variable, from the state (own rows, transmissive
-// ghost rows) or from the neighbour's row strip (halo rows); Dirichlet ghost
-// rows are constants.  The halo lanes 0 and 31 fetch only the one cell the
-// task's faces use (lane 0's last, lane 31's first); their other slots keep
-// whatever they held, which only feeds results those lanes never store.
-// Lanes of a ragged last strip that reach past the grid go cell by cell.
+// Own row j of a lane of a ragged last strip whose cells reach past the
+// grid, cell by cell: columns inside the grid from the state, the ghost
+// column nx from the boundary condition (the first column's cell of the
+// west column strip of the task at the start of the row, across the
+// periodic side; the task's own last column; or the prescribed state), the
+// cells past it (which no face uses) from the same source.
+template <class A, int V, int NV, int D, class G>
+static __device__ __forceinline__ void lring_issue_cells(const G &a, const typename Ops<A>::S *W, int X,
+                                                         const Ovl<typename Ops<A>::S> &o,
+                                                         const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
+                                                         int slot, int j) {
+  using S = typename Ops<A>::S;
+  constexpr int N = V * Ops<A>::K, SW = 30 * N;
+  using L = OvlLayout<NV, N, SW>;
+  const S *g;
+  long long gvs;
+  if (a.bc[kE] == kPeriodic) {
+    g = o.rd + (long long)(o.cy * o.nstrips) * o.ts + L::colW(o.ty) + (j - o.y0) * N;
+    gvs = (long long)o.ty * N;
+  } else if (a.bc[kE] == kDirichlet) {
+    g = o.dstrip + kE * NV * N;
+    gvs = N;
+  } else {
+    g = W + (long long)j * a.pitch + (a.nx - 1);
+    gvs = a.plane;
+  }
+  const S *row = W + (long long)j * a.pitch;
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const bool in = X + c < a.nx;
+    const S *q = in ? row + X + c : g;
+    const long long vs = in ? a.plane : gvs;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      S *d = rg.slot(slot, v) + c;
+      if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, q + v * vs);
+      else *d = __ldcg(q + v * vs);
+    }
+  }
+}
+
+// In-place counterpart of lring_issue.  A lane copies one vector of N cells
+// per variable from the source ovl_halo_src (halo rows) or ovl_lane_setup
+// (own rows) gives: its own cells of the state, a neighbour's column or row
+// strip, or the prescribed state's cells; only the own rows of the lanes of
+// a ragged last strip that reach past the grid go cell by cell.
 template <class A, int V, int NV, int D, class G>
 static __device__ __forceinline__ void lring_issue_inplace(const G &a, const typename Ops<A>::S *W, int X,
                                                            const Ovl<typename Ops<A>::S> &o,
                                                            const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
                                                            int r, int j) {
   using S = typename Ops<A>::S;
-  constexpr int N = V * Ops<A>::K, SW = 30 * N;
+  constexpr int N = V * Ops<A>::K;
   const int slot = r % D;
-  const int lane = threadIdx.x & 31;
-  const bool halo_lane = lane == 0 || lane == 31;
-  const int c0 = lane == 0 ? N - 1 : 0;  // the halo lanes' used cell
-  if (j >= o.y0 && j < o.y1) {
-    // an own row (warp-uniform): the state for lanes 1..30, and for the halo
-    // lanes the source found once per task, advanced by the row
-    const int jr = j - o.y0;
-    if (halo_lane) {
-      const S *q = o.hp + (o.hkind == 2 ? (long long)jr : (long long)jr * a.pitch);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        S *d = rg.slot(slot, v) + c0;
-        if (o.hdir >= 0) *d = (S)a.bc_state[o.hdir][v];
-        else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, q + v * o.hvs);
-        else *d = __ldcg(q + v * o.hvs);
-      }
-      cp_async_commit();
-      return;
-    }
-    if (X + N <= a.nx) {
-      const S *q = W + (long long)j * a.pitch + X;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), q + v * a.plane);
-      cp_async_commit();
-      return;
-    }
-  }
-  long long vs;
-  int dir, kind;
-  const S *p = inplace_cell<NV, SW>(a, W, o, j, X + c0, vs, dir, kind);
-  if (halo_lane) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      S *d = rg.slot(slot, v) + c0;
-      if (dir >= 0) *d = (S)a.bc_state[dir][v];
-      else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, p + v * vs);
-      else *d = __ldcg(p + v * vs);
-    }
-  } else if (dir >= 0) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-      for (int c = 0; c < N; ++c) rg.slot(slot, v)[c] = (S)a.bc_state[dir][v];
-  } else if (X + N <= a.nx && kind != 2) {
+  if (j < o.y0 || j >= o.y1) {
+    long long vs;
+    const S *p = ovl_halo_src<NV, N>(a, W, o, X, j, vs);
 #pragma unroll
     for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * vs);
+  } else if (o.flags & kPercell) {
+    lring_issue_cells<A, V, NV, D>(a, W, X, o, rg, slot, j);
   } else {
-#pragma unroll 1
-    for (int c = 0; c < N; ++c) {
-      const S *q = inplace_cell<NV, SW>(a, W, o, j, X + c, vs, dir, kind);
+    const S *p = o.op + (long long)(j - o.y0) * o.ors;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        S *d = rg.slot(slot, v) + c;
-        if (dir >= 0) *d = (S)a.bc_state[dir][v];
-        else if (sizeof(S) >= 4) cp_async_cells<S, 1>(d, q + v * vs);
-        else *d = __ldcg(q + v * vs);
-      }
-    }
+    for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * o.ovs);
   }
   cp_async_commit();
 }
@@ -991,8 +1016,13 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
   }
   RowState<A, V, NV> RA, RB;
   A Fs[V][NV];
+  const int lane = threadIdx.x & 31;
+  auto read = [&](int r, A(&W)[V][NV]) {
+    lring_read<A, V, NV, D>(rg, r, W);
+    if constexpr (INPL) ovl_fix_cols<A, V, NV>(a, *ovl, W, lane);
+  };
   cp_async_wait<D - 2>();
-  lring_read<A, V, NV, D>(rg, 0, RA.W);
+  read(0, RA.W);
 #pragma unroll
   for (int c = 0; c < V; ++c) {
     A Fx_[NV], sx_;
@@ -1001,7 +1031,7 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
   if (D - 1 < nrows) issue(D - 1, y0 - 1 + D - 1);
   else cp_async_commit();
   cp_async_wait<D - 2>();
-  lring_read<A, V, NV, D>(rg, 1, RB.W);
+  read(1, RB.W);
   row_x<Sys, V>(P, RB.W, RB.Fy, RB.sy, RB.dX);
   if (D < nrows) issue(D, y0 - 1 + D);
   else cp_async_commit();
@@ -1017,7 +1047,7 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
     {
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
-      lring_read<A, V, NV, D>(rg, r, RA.W);
+      read(r, RA.W);
       advance_row<Sys, A, V, false, FIN, INPL>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad, xin, ovl);
       if (r + D - 1 < nrows) issue(r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
@@ -1027,7 +1057,7 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
     {
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
-      lring_read<A, V, NV, D>(rg, r, RB.W);
+      read(r, RB.W);
       advance_row<Sys, A, V, false, FIN, INPL>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad, xin, ovl);
       if (r + D - 1 < nrows) issue(r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
@@ -1108,8 +1138,7 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
       const int y1 = min(y0 + ty, a.ny);
       // warp-uniform: does every lane of the strip read real columns only?
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
-      if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (D < 0 && INPL) {
+      if constexpr (INPL && D < 0) {
         Ovl<S> o;
         o.rd = a.ovl[n & 1];
         o.wr = a.ovl[(n + 1) & 1];
@@ -1122,11 +1151,15 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
         o.y1 = y1;
         o.ty = TY;
         o.ts = a.ovl_task;
+        o.dstrip = a.ovl_bc;
         ovl_lane_setup<NV, N>(a, src, o, X, lane);
         march_async<Sys, A, V, DA, FIN, true>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad, &o);
-      } else if (D < 0) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);
-      else if (xin) march<Sys, A, V, true, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
-      else march<Sys, A, V, false, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      } else {
+        if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
+        else if (D < 0) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);
+        else if (xin) march<Sys, A, V, true, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+        else march<Sys, A, V, false, FIN>(a, P, src, dst, X, y0, y1, writer, lx, ly, lam_loc, bad);
+      }
     }
   }
 
@@ -1135,12 +1168,25 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
 }
 
 // In-place mode: the overlap strips of one parity from the state itself,
-// after the host loaded or moved the state (layout of OvlLayout; cells past
-// the grid are left alone, nothing reads them as data).
+// after the host loaded or moved the state (layout of OvlLayout; cells of a
+// strip past the task's last column get that column's values, so every
+// strip cell is a finite state value).
+// In-place mode: the prescribed state of each side as stored cells,
+// [side][variable][n cells] (converted to the storage type exactly as the
+// ring's Dirichlet ghosts are).
+template <class S> struct BcCells {
+  typename ParamOf<S>::T v[4][8];
+};
+template <class S>
+__global__ void fill_bc_cells_kernel(BcCells<S> bc, int nv, int n, S *dst) {
+  const int k = threadIdx.x;
+  if (k < 4 * nv * n) dst[k] = (S)bc.v[k / (nv * n)][(k / n) % nv];
+}
+
 template <class S>
 __global__ void fill_ovl_kernel(const S *W, int nx, int ny, long long pitch, long long plane, int nv,
-                                int nstrips, int nchunks, int ty, int sw, int ts, S *ovl) {
-  const long long per = (long long)nv * (2 * ty + 2 * sw);
+                                int nstrips, int nchunks, int ty, int n, int sw, int ts, S *ovl) {
+  const long long per = (long long)nv * (2 * ty * n + 2 * sw);
   const long long total = (long long)nstrips * nchunks * per;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
@@ -1150,19 +1196,21 @@ __global__ void fill_ovl_kernel(const S *W, int nx, int ny, long long pitch, lon
     const int X0 = sx * sw, y0 = cy * ty, y1 = min(y0 + ty, ny);
     const int last = min(X0 + sw, nx) - 1;
     int j, col, v;
-    if (e < 2 * nv * ty) {
-      const int which = e / (nv * ty), rem = e % (nv * ty);
-      v = rem / ty;
-      j = y0 + rem % ty;
-      col = which == 0 ? X0 : last;
-      if (j >= y1) continue;
+    if (e < 2 * nv * ty * n) {
+      // column strips: west = the task's first n columns, east = its last n
+      const int which = e / (nv * ty * n), rem = e % (nv * ty * n);
+      v = rem / (ty * n);
+      const int rc = rem % (ty * n);
+      j = y0 + rc / n;
+      const int c = rc % n;
+      col = which == 0 ? min(X0 + c, last) : max(last - (n - 1 - c), X0);
+      if (j >= y1) j = y1 - 1;
     } else {
-      const int e2 = e - 2 * nv * ty;
+      const int e2 = e - 2 * nv * ty * n;
       const int which = e2 / (nv * sw), rem = e2 % (nv * sw);
       v = rem / sw;
-      col = X0 + rem % sw;
+      col = min(X0 + rem % sw, last);
       j = which == 0 ? y0 : y1 - 1;
-      if (col > last) continue;
     }
     ovl[(long long)t * ts + e] = W[(long long)v * plane + (long long)j * pitch + col];
   }

@@ -114,8 +114,10 @@ def test_inplace_frees_the_second_buffer():
         free0, _ = torch.cuda.mem_get_info()
         s.set_inplace(True)
         free1, _ = torch.cuda.mem_get_info()
-        # 256 MiB of state freed, about 6% of it taken back by the strips
-        assert free1 - free0 > 200 * 2 ** 20, (free0, free1)
+        # 256 MiB of state freed, about 28% of it taken back by the strips
+        # (two parities of four border strips per warp task; the column
+        # strips hold the four cells of a halo lane per row)
+        assert free1 - free0 > 160 * 2 ** 20, (free0, free1)
         s.run(3)
 
 
