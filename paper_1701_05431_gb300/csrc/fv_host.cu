@@ -316,9 +316,12 @@ static void free_graphs(fv_ctx *c) {
 // kernel, so that a task's time follows its rows (measured: 4.35 against
 // 4.07 G cell-updates/s on the 2048^2 four-quadrant case, 1.66 against 0.91
 // on 128^2 advection, where one wave of 4-row tasks replaces 16-row ones).
-// The FP32 and BF16 kernels are bound by HBM bandwidth, which a last partial
-// wave of warps still draws; balanced rows made them slower (170 against 175
-// G on 8192^2), so they keep TY.
+// The FP32 and BF16 kernels are bound by HBM bandwidth on large grids, which
+// a last partial wave of warps still draws; balanced rows made them slower
+// there (170 against 175 G on 8192^2), so from 2^24 cells on they keep TY.
+// Below that the state sits in or near L2 and a launch's last partial wave
+// is what costs: balanced rows give the fastest candidate on the 2048^2
+// four-quadrant case 108 against 104 G cell-updates/s.
 static int balanced_rows(const fv_ctx *c, const Variant &V, int nb) {
   return balance_rows_for(V, c->cfg.nx, c->cfg.ny, (long long)nb * V.NW * c->sms, nullptr);
 }
@@ -330,7 +333,8 @@ static fv_status select_variant(fv_ctx *c, int vi) {
     FV_CUDA(c, cudaFuncSetAttribute(V.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
   FV_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, V.kernel, V.NW * 32, V.smem));
   if (nb < 1) return fail(c, FV_ERR_CUDA, std::string("kernel cannot launch: ") + V.desc);
-  c->ty = (V.inplace || V.tb || V.precision != 0) ? V.TY : balanced_rows(c, V, nb);
+  const bool small = (long long)c->cfg.nx * c->cfg.ny < (1LL << 24);
+  c->ty = (V.inplace || V.tb || (V.precision != 0 && !small)) ? V.TY : balanced_rows(c, V, nb);
   const int nstrips = (c->cfg.nx + 30 * V.V - 1) / (30 * V.V);
   const int nchunks = (c->cfg.ny + c->ty - 1) / c->ty;
   const long long ntasks = (long long)nstrips * nchunks;
