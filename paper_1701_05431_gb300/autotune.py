@@ -1,7 +1,7 @@
 """Autotuner: time every compiled kernel candidate on each configuration and
 record the fastest per (system, precision, grid-size class, mode).
 
-  python -m paper_1701_05431_gb300.autotune [--out-dir DIR] [--only NAME ...]
+  python -m paper_1701_05431_gb300.autotune [--out-dir DIR] [--only NAME ...] [--merge TABLE.json]
 
 For each configuration below it builds the seeded synthetic input, and for
 every candidate of the configuration's mode (two state buffers, in place, two
@@ -167,6 +167,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--out-dir", default=None)
     ap.add_argument("--only", nargs="*", default=None, help="configuration names to tune (default: all)")
+    ap.add_argument("--merge", default=None,
+                    help="an existing tune_table.json whose other configurations are kept in the table written")
     a = ap.parse_args(argv)
     import torch
     from paper_1701_05431_gb300 import fvlib
@@ -190,6 +192,11 @@ def main(argv=None):
         results.append(r)
         best = max(cand, key=lambda kv: kv[1])
         print(json.dumps({"name": name, "best": best[0], "rate": best[1], "candidates": len(cand)}), flush=True)
+    if a.merge:
+        with open(a.merge) as f:
+            kept = [r for r in json.load(f) if r["name"] not in {x["name"] for x in results}]
+        order = [c[0] for c in configurations()]
+        results = sorted(kept + results, key=lambda r: order.index(r["name"]) if r["name"] in order else len(order))
     inc = os.path.join(a.out_dir or os.path.join(HERE, "csrc"), "fv_tune_table.inc")
     js = os.path.join(a.out_dir or HERE, "tune_table.json")
     write_table(results, inc, js)

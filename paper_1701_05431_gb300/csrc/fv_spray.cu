@@ -53,13 +53,17 @@ template <class R> struct SourceArgs {
   int ug_mode, Q;
 };
 
-// Moments M_k = sum_q w_q 2 x_q x_q^k n(x_q^2), k = 0..6, and
-// M_{-1} = sum_q 2 w_q n(x_q^2) (= m_{-1/2}) of the trial density; the values
-// e_q = n(x_q^2) are left in e[q * es] (es: the thread stride of the cache).
+// Moments M_k = sum_q w_q 2 x_q x_q^k n(x_q^2) of the trial density, in
+// three passes over the nodes so that no solve computes a moment it does not
+// use: M_0..M_3 with the values e_q = n(x_q^2), which every evaluation needs
+// (the residual); M_4..M_6 from the cached e_q, only before a Newton step
+// (the Hessian); M_{-1} = sum_q 2 w_q n(x_q^2) (= m_{-1/2}) once, at the
+// solution.  Each moment is the same FMA sequence in node order whichever
+// pass computes it.  e: the thread's exponential cache (stride es).
 static __device__ __forceinline__ void me_moments(const double *nd, int Q, const double (&lam)[4],
                                                   double (&M)[8], double *e, int es) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) M[k] = 0.0;
+  for (int k = 0; k < 4; ++k) M[k] = 0.0;
   for (int q = 0; q < Q; ++q) {
     const double *r = nd + q * kNodeStride;
     const double x = r[0];
@@ -67,9 +71,28 @@ static __device__ __forceinline__ void me_moments(const double *nd, int Q, const
     const double eq = exp(-poly);
     e[q * es] = eq;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) M[k] = fma(r[1 + k], eq, M[k]);
-    M[7] = fma(r[8], eq, M[7]);
+    for (int k = 0; k < 4; ++k) M[k] = fma(r[1 + k], eq, M[k]);
   }
+}
+
+// M_4..M_6 (the rest of the Hessian) from the cached e_q.
+static __device__ __forceinline__ void me_moments_hessian(const double *nd, int Q, double (&M)[8], const double *e,
+                                                          int es) {
+#pragma unroll
+  for (int k = 4; k < 7; ++k) M[k] = 0.0;
+  for (int q = 0; q < Q; ++q) {
+    const double *r = nd + q * kNodeStride;
+    const double eq = e[q * es];
+#pragma unroll
+    for (int k = 4; k < 7; ++k) M[k] = fma(r[1 + k], eq, M[k]);
+  }
+}
+
+// M_{-1} = m_{-1/2} from the cached e_q.
+static __device__ __forceinline__ double me_moment_minus_half(const double *nd, int Q, const double *e, int es) {
+  double s = 0.0;
+  for (int q = 0; q < Q; ++q) s = fma(nd[q * kNodeStride + 8], e[q * es], s);
+  return s;
 }
 
 // Incremental updates of the cached exponentials: exp(-t) from its Taylor
@@ -101,14 +124,14 @@ static __device__ __forceinline__ double exp_neg_small(double t) {
   return p;
 }
 
-// The moments after the multipliers moved by d, from the cached e_q of the
+// M_0..M_3 after the multipliers moved by d, from the cached e_q of the
 // previous multipliers: e_q <- e_q exp(-(d0 + d1 x + d2 x^2 + d3 x^3)).
 // Requires |d0| + |d1| + |d2| + |d3| <= the bound of degree DEG.
 template <int DEG>
 static __device__ __forceinline__ void me_moments_step(const double *nd, int Q, const double (&d)[4],
                                                        double (&M)[8], double *e, int es) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) M[k] = 0.0;
+  for (int k = 0; k < 4; ++k) M[k] = 0.0;
   for (int q = 0; q < Q; ++q) {
     const double *r = nd + q * kNodeStride;
     const double x = r[0];
@@ -116,8 +139,7 @@ static __device__ __forceinline__ void me_moments_step(const double *nd, int Q, 
     const double eq = e[q * es] * exp_neg_small<DEG>(pd);
     e[q * es] = eq;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) M[k] = fma(r[1 + k], eq, M[k]);
-    M[7] = fma(r[8], eq, M[7]);
+    for (int k = 0; k < 4; ++k) M[k] = fma(r[1 + k], eq, M[k]);
   }
 }
 
@@ -192,6 +214,7 @@ static __device__ bool maxent(const double *nd, int Q, double tol, const double 
       break;
     }
     if (!(worst == worst)) return false;
+    me_moments_hessian(nd, Q, M, e, es);
     if (!spd_solve4(M, r, d)) return false;
     if (worst >= 1e-3) {
       // far from the solution: halve the step until the dual
@@ -226,7 +249,7 @@ static __device__ bool maxent(const double *nd, int Q, double tol, const double 
       if (!(fabs(M[k] - m[k]) <= 1e-10 * m[k])) return false;
   }
   n0 = exp(-lam[0]);
-  mmh = M[7];
+  mmh = me_moment_minus_half(nd, Q, e, es);
   return true;
 }
 
