@@ -72,6 +72,7 @@ def configurations():
         ("c3_bf16", "euler 8192^2 smooth periodic", "euler", "bf16", "single", c3, 20, 3),
         ("c3_inplace_f32", "euler 8192^2 smooth periodic", "euler", "f32", "inplace", c3, 20, 3),
         ("c3_inplace_f64", "euler 8192^2 smooth periodic", "euler", "f64", "inplace", c3, 4, 1),
+        ("c3_inplace_bf16", "euler 8192^2 smooth periodic", "euler", "bf16", "inplace", c3, 20, 3),
         ("c3_two_step_f32", "euler 8192^2 smooth periodic, fixed dt", "euler", "f32", "two-step", c3f, 20, 4),
         ("c3_two_step_bf16", "euler 8192^2 smooth periodic, fixed dt", "euler", "bf16", "two-step", c3f, 20, 4),
         ("c4", "512 batched euler four-quadrant instances", "euler", "f32", "batch", None, 40, 4),

@@ -300,21 +300,23 @@ static __device__ __forceinline__ void row_x(const SysParams<A> &P, const A (&W)
 // value another task is overwriting.  A task's own rows are read (through
 // the ring, several rows ahead) before it overwrites them.
 template <class S> struct Ovl {
-  const S *rd;     // strips of parity n % 2 (borders of W^n)
-  S *wr;           // strips of parity (n + 1) % 2 (borders of W^{n+1})
-  int sx, cy;      // this task's strip and chunk
-  int nstrips, nchunks;
-  int X0, y0, y1;  // first column, first and end row of the task
-  int ty, ts;      // rows per task, elements per task in one parity
-  // per lane, set once per task by ovl_lane_setup
-  const S *op;     // own rows: source of row y0 (the state, or a neighbour's column strip)
-  int ors;         // its row stride
-  long long ovs;   // its variable stride
+  const S *op;     // own rows: source of row y0 (the state, a neighbour's column strip, or prescribed cells)
+  int task;        // the warp task: strip task % nstrips, chunk task / nstrips
+  int y0, y1;      // first and end row of the task
+  unsigned flags;  // kPercell | fixW (bits 1-2) | fixE (bits 3-4) | kLastFull | own-row source kind | kOdd
+  // kept only with fewer than four cells per lane (see ovl_opaque)
+  int sx, cy;      // the task's strip and chunk
+  int ors;         // row stride of op
+  long long ovs;   // variable stride of op
+  const S *rd;     // strips of parity n % 2
   S *wb;           // this task's strips of parity (n + 1) % 2
-  const S *dstrip; // the prescribed states of the four sides as stored cells: [side][variable][N cells]
-  unsigned flags;  // kPercell | fixW (bits 1-2) | fixE (bits 3-4) | kLastFull
 };
-enum : unsigned { kPercell = 1u, kFixWShift = 1, kFixEShift = 3, kLastFull = 32u };
+// kOwnStrip: own rows from a column strip (row stride N, variable stride ty N);
+// kOwnDir: from the prescribed cells (row stride 0, variable stride N);
+// neither: from the state (pitch, plane).  kOdd: the step is odd, so the
+// strips of W^n are those of parity 1.
+enum : unsigned { kPercell = 1u, kFixWShift = 1, kFixEShift = 3, kLastFull = 32u, kOwnStrip = 64u, kOwnDir = 128u,
+                  kOdd = 256u };
 
 // Element offsets inside one task's strips (NV variables each).
 template <int NV, int N, int SW> struct OvlLayout {
@@ -324,55 +326,80 @@ template <int NV, int N, int SW> struct OvlLayout {
   static __device__ __forceinline__ int rowN(int ty) { return 2 * NV * ty * N + NV * SW; }
 };
 
+// The strips of W^n (read) and of W^{n+1} (written) this step.  With four
+// or more cells per lane the march has no registers to spare, so the task
+// index passes through an opaque copy where a value is derived per row: the
+// compiler then recomputes the few integer operations instead of keeping
+// loop-invariant pointers in registers.  With fewer cells it keeps them.
+template <int N> static __device__ __forceinline__ int ovl_opaque(int x) {
+  if constexpr (N < 4) return x;
+  int y;
+  asm volatile("mov.b32 %0, %1;" : "=r"(y) : "r"(x));
+  return y;
+}
+template <int N, class G, class S> static __device__ __forceinline__ const S *ovl_rd(const G &a, const Ovl<S> &o) {
+  if constexpr (N < 4) return o.rd;
+  return (o.flags & kOdd) ? a.ovl[1] : a.ovl[0];
+}
+template <int N, class G, class S> static __device__ __forceinline__ S *ovl_wb(const G &a, const Ovl<S> &o) {
+  if constexpr (N < 4) return o.wb;
+  return ((o.flags & kOdd) ? a.ovl[0] : a.ovl[1]) + (long long)ovl_opaque<N>(o.task) * a.ovl_task;
+}
+
 // Per-lane in-place bookkeeping of one task: where the lane's N cells of the
 // task's own rows come from, whether a ghost column has to be set after a
-// read, and where the task's strips of the next parity go.  Lanes 1..30 read
+// read, and whether the strip reaches past the grid.  Lanes 1..30 read
 // their own cells from the state; the halo lanes read the neighbouring
 // task's column strip (periodic sides: the task across the boundary), on a
 // Dirichlet side the prescribed state's cells, and on a transmissive side
 // some of their own task's cells, the ghost being set in registers
 // (ovl_fix_cols).  Lanes of a ragged last strip that reach past the grid go
 // cell by cell.
-template <int NV, int N, class G, class S>
-static __device__ __forceinline__ void ovl_lane_setup(const G &a, const S *W, Ovl<S> &o, int X, int lane) {
+template <int NV, int N, int TY, class G, class S>
+static __device__ __forceinline__ void ovl_lane_setup(const G &a, const S *W, Ovl<S> &o, int X, int lane, int sx,
+                                                      int cy, long long n) {
   constexpr int SW = 30 * N;
   using L = OvlLayout<NV, N, SW>;
-  const bool full = o.X0 + SW <= a.nx;  // every column of the strip lies in the grid
+  const int X0 = sx * SW;
+  const bool full = X0 + SW <= a.nx;  // every column of the strip lies in the grid
   unsigned f = (lane >= 1 && X + N > a.nx) ? kPercell : 0u;
+  if (n & 1) f |= kOdd;
+  const S *rd = (n & 1) ? a.ovl[1] : a.ovl[0];
   o.op = W + (long long)o.y0 * a.pitch + X;
-  o.ors = (int)a.pitch;
-  o.ovs = a.plane;
   if (lane == 0) {
-    if (o.sx > 0 || a.bc[kW] == kPeriodic) {
-      o.op = o.rd + (long long)(o.cy * o.nstrips + (o.sx > 0 ? o.sx - 1 : o.nstrips - 1)) * o.ts + L::colE(o.ty);
-      o.ors = N;
-      o.ovs = (long long)o.ty * N;
+    if (sx > 0 || a.bc[kW] == kPeriodic) {
+      o.op = rd + (long long)(cy * a.nstrips + (sx > 0 ? sx - 1 : a.nstrips - 1)) * a.ovl_task + L::colE(TY);
+      f |= kOwnStrip;
     } else if (a.bc[kW] == kDirichlet) {
-      o.op = o.dstrip + kW * NV * N;  // the same N cells every row
-      o.ors = 0;
-      o.ovs = N;
+      o.op = a.ovl_bc + kW * NV * N;  // the same N cells every row
+      f |= kOwnDir;
     } else {
-      o.op = W + (long long)o.y0 * a.pitch + o.X0;
+      o.op = W + (long long)o.y0 * a.pitch + X0;
     }
   } else if (lane == 31 && !(f & kPercell)) {
-    if (o.sx < o.nstrips - 1 || a.bc[kE] == kPeriodic) {
-      o.op = o.rd + (long long)(o.cy * o.nstrips + (o.sx < o.nstrips - 1 ? o.sx + 1 : 0)) * o.ts + L::colW(o.ty);
-      o.ors = N;
-      o.ovs = (long long)o.ty * N;
+    if (sx < a.nstrips - 1 || a.bc[kE] == kPeriodic) {
+      o.op = rd + (long long)(cy * a.nstrips + (sx < a.nstrips - 1 ? sx + 1 : 0)) * a.ovl_task + L::colW(TY);
+      f |= kOwnStrip;
     } else if (a.bc[kE] == kDirichlet) {
-      o.op = o.dstrip + kE * NV * N;
-      o.ors = 0;
-      o.ovs = N;
+      o.op = a.ovl_bc + kE * NV * N;
+      f |= kOwnDir;
     } else {
       o.op = W + (long long)o.y0 * a.pitch + (X - N);
     }
   }
   // transmissive west or east side: the halo lane's ghost cell is a copy of the border column
-  if (o.sx == 0 && a.bc[kW] == kTransmissive) f |= 1u << kFixWShift;
-  if (full && o.sx == o.nstrips - 1 && a.bc[kE] == kTransmissive) f |= 1u << kFixEShift;
+  if (sx == 0 && a.bc[kW] == kTransmissive) f |= 1u << kFixWShift;
+  if (full && sx == a.nstrips - 1 && a.bc[kE] == kTransmissive) f |= 1u << kFixEShift;
   if (full) f |= kLastFull;
   o.flags = f;
-  o.wb = o.wr + (long long)(o.cy * o.nstrips + o.sx) * o.ts;
+  if constexpr (N < 4) {
+    o.sx = sx;
+    o.cy = cy;
+    o.ors = (f & kOwnStrip) ? N : (f & kOwnDir) ? 0 : (int)a.pitch;
+    o.ovs = (f & kOwnStrip) ? (long long)TY * N : (f & kOwnDir) ? (long long)N : a.plane;
+    o.rd = rd;
+    o.wb = ((n & 1) ? a.ovl[0] : a.ovl[1]) + (long long)o.task * a.ovl_task;
+  }
 }
 
 // Source of a lane's N cells of halo row j (j = y0 - 1 or y1), always a
@@ -382,31 +409,33 @@ static __device__ __forceinline__ void ovl_lane_setup(const G &a, const S *W, Ov
 // prescribed state's cells.  The halo lanes' cells there are tile corners no
 // face uses: they read the strip at lane 1's or lane 30's position, and so
 // do the lanes of a ragged last strip past the grid.
-template <int NV, int N, class G, class S>
-static __device__ __forceinline__ const S *ovl_halo_src(const G &a, const S *W, const Ovl<S> &o, int X, int j,
-                                                        long long &vs) {
+template <int NV, int N, int TY, class G, class S>
+static __device__ __forceinline__ const S *ovl_halo_src(const G &a, const Ovl<S> &o, int X, int j, long long &vs) {
   constexpr int SW = 30 * N;
   using L = OvlLayout<NV, N, SW>;
-  const int xo = min(max(X - o.X0, 0), SW - N);
+  const int task = ovl_opaque<N>(o.task);
+  const int sx = N < 4 ? o.sx : task % a.nstrips, cy = N < 4 ? o.cy : task / a.nstrips;
+  const int xo = min(max(X - sx * SW, 0), SW - N);
+  const S *rd = ovl_rd<N>(a, o);
   vs = SW;
   if (j < o.y0) {
-    if (o.cy > 0 || a.bc[kS] == kPeriodic)
-      return o.rd + (long long)((o.cy > 0 ? o.cy - 1 : o.nchunks - 1) * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + xo;
+    if (cy > 0 || a.bc[kS] == kPeriodic)
+      return rd + (long long)((cy > 0 ? cy - 1 : a.nchunks - 1) * a.nstrips + sx) * a.ovl_task + L::rowN(TY) + xo;
     if (a.bc[kS] == kDirichlet) {
       vs = N;
-      return o.dstrip + kS * NV * N;
+      return a.ovl_bc + kS * NV * N;
     }
     // transmissive: the task's own first row, as its south row strip holds it
-    return o.rd + (long long)(o.cy * o.nstrips + o.sx) * o.ts + L::rowS(o.ty) + xo;
+    return rd + (long long)task * a.ovl_task + L::rowS(TY) + xo;
   }
-  if (o.cy < o.nchunks - 1 || a.bc[kN] == kPeriodic)
-    return o.rd + (long long)((o.cy < o.nchunks - 1 ? o.cy + 1 : 0) * o.nstrips + o.sx) * o.ts + L::rowS(o.ty) + xo;
+  if (cy < a.nchunks - 1 || a.bc[kN] == kPeriodic)
+    return rd + (long long)((cy < a.nchunks - 1 ? cy + 1 : 0) * a.nstrips + sx) * a.ovl_task + L::rowS(TY) + xo;
   if (a.bc[kN] == kDirichlet) {
     vs = N;
-    return o.dstrip + kN * NV * N;
+    return a.ovl_bc + kN * NV * N;
   }
   // transmissive: the task's own last row, as its north row strip holds it
-  return o.rd + (long long)(o.cy * o.nstrips + o.sx) * o.ts + L::rowN(o.ty) + xo;
+  return rd + (long long)task * a.ovl_task + L::rowN(TY) + xo;
 }
 
 // Ghost columns of a row just read, on a transmissive west or east side
@@ -439,35 +468,38 @@ static __device__ __forceinline__ void ovl_fix_cols(const G &a, const Ovl<S> &o,
 // the lane holding the task's last column puts it in cell N - 1 of the east
 // column strip), values of W^{n+1} in storage type, t[v][c] for the lane's
 // N cells.
-template <int NV, int N, class G, class S>
+template <int NV, int N, int TY, class G, class S>
 static __device__ __forceinline__ void write_strips(const G &a, const Ovl<S> &o, int X, int j, const S (&t)[NV][N]) {
   constexpr int SW = 30 * N;
   using L = OvlLayout<NV, N, SW>;
+  const int lane = threadIdx.x & 31;
+  const int xo = (lane - 1) * N;  // X minus the strip's first column
   if (j == o.y0 || j == o.y1 - 1) {
+    S *wb = ovl_wb<N>(a, o);
     // a one-row task writes its row to both row strips
-    const int first = j == o.y0 ? L::rowS(o.ty) : L::rowN(o.ty);
+    const int first = j == o.y0 ? L::rowS(TY) : L::rowN(TY);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + first + v * SW + (X - o.X0), t[v]);
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(wb + first + v * SW + xo, t[v]);
     if (o.y1 - o.y0 == 1) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) VecIO<S, N>::st(o.wb + L::rowN(o.ty) + v * SW + (X - o.X0), t[v]);
+      for (int v = 0; v < NV; ++v) VecIO<S, N>::st(wb + L::rowN(TY) + v * SW + xo, t[v]);
     }
   }
   const int jr = j - o.y0;
-  const int lane = threadIdx.x & 31;
   const bool full = (o.flags & kLastFull) != 0u;
   if (lane == 1 || (full && lane == 30)) {
-    S *cs = o.wb + (lane == 1 ? L::colW(o.ty) : L::colE(o.ty)) + jr * N;
+    S *cs = ovl_wb<N>(a, o) + (lane == 1 ? L::colW(TY) : L::colE(TY)) + jr * N;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(cs + (long long)v * o.ty * N, t[v]);
+    for (int v = 0; v < NV; ++v) VecIO<S, N>::st(cs + (long long)v * TY * N, t[v]);
   }
   if (!full) {
-    const int ecell = min(o.X0 + SW, a.nx) - 1 - X;  // the task's last column, if this lane holds it
+    const int ecell = min(X - xo + SW, a.nx) - 1 - X;  // the task's last column, if this lane holds it
+    S *wb = ovl_wb<N>(a, o);
 #pragma unroll
     for (int c = 0; c < N; ++c)
       if (c == ecell) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) o.wb[L::colE(o.ty) + v * o.ty * N + jr * N + (N - 1)] = t[v][c];
+        for (int v = 0; v < NV; ++v) wb[L::colE(TY) + v * TY * N + jr * N + (N - 1)] = t[v][c];
       }
   }
 }
@@ -483,7 +515,7 @@ template <class A, int V, int NV> struct RowState {
 // Compute part of one row of the march (rows j and j+1 in registers): x-work
 // of row j+1, the y-face between rows j and j+1 evaluated once, update and
 // store of row j (by the writer lanes), and the new state's wave speed.
-template <class Sys, class A, int V, bool XIN, bool FIN, bool INPL = false, class G>
+template <class Sys, class A, int V, bool XIN, bool FIN, bool INPL = false, int TYC = 0, class G>
 static __device__ __forceinline__ void advance_row(const G &a, const SysParams<A> &P,
                                                    typename Ops<A>::S *dst_lane, int X, int j,
                                                    bool writer, A lx, A ly, RowState<A, V, Sys::NV> &cur,
@@ -530,7 +562,7 @@ static __device__ __forceinline__ void advance_row(const G &a, const SysParams<A
         for (int c = 0; c < N; ++c)
           if (X + c < a.nx) __stcs(row + v * a.plane + c, t[v][c]);
     }
-    if (INPL) write_strips<NV, N>(a, *ovl, X, j, t);
+    if constexpr (INPL) write_strips<NV, N, TYC>(a, *ovl, X, j, t);
     if (FIN) {
 #pragma unroll
       for (int c = 0; c < V; ++c) {
@@ -890,7 +922,7 @@ static __device__ __forceinline__ void lring_issue(const G &a,
 // west column strip of the task at the start of the row, across the
 // periodic side; the task's own last column; or the prescribed state), the
 // cells past it (which no face uses) from the same source.
-template <class A, int V, int NV, int D, class G>
+template <class A, int V, int NV, int D, int TY, class G>
 static __device__ __forceinline__ void lring_issue_cells(const G &a, const typename Ops<A>::S *W, int X,
                                                          const Ovl<typename Ops<A>::S> &o,
                                                          const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
@@ -901,10 +933,12 @@ static __device__ __forceinline__ void lring_issue_cells(const G &a, const typen
   const S *g;
   long long gvs;
   if (a.bc[kE] == kPeriodic) {
-    g = o.rd + (long long)(o.cy * o.nstrips) * o.ts + L::colW(o.ty) + (j - o.y0) * N;
-    gvs = (long long)o.ty * N;
+    // the first task of this chunk (strip 0): task - task % nstrips
+    const int task = ovl_opaque<N>(o.task);
+    g = ovl_rd<N>(a, o) + (long long)(task - task % a.nstrips) * a.ovl_task + L::colW(TY) + (j - o.y0) * N;
+    gvs = (long long)TY * N;
   } else if (a.bc[kE] == kDirichlet) {
-    g = o.dstrip + kE * NV * N;
+    g = a.ovl_bc + kE * NV * N;
     gvs = N;
   } else {
     g = W + (long long)j * a.pitch + (a.nx - 1);
@@ -930,7 +964,7 @@ static __device__ __forceinline__ void lring_issue_cells(const G &a, const typen
 // (own rows) gives: its own cells of the state, a neighbour's column or row
 // strip, or the prescribed state's cells; only the own rows of the lanes of
 // a ragged last strip that reach past the grid go cell by cell.
-template <class A, int V, int NV, int D, class G>
+template <class A, int V, int NV, int D, int TY, class G>
 static __device__ __forceinline__ void lring_issue_inplace(const G &a, const typename Ops<A>::S *W, int X,
                                                            const Ovl<typename Ops<A>::S> &o,
                                                            const LaneRing<typename Ops<A>::S, V * Ops<A>::K, NV, D> &rg,
@@ -940,15 +974,24 @@ static __device__ __forceinline__ void lring_issue_inplace(const G &a, const typ
   const int slot = r % D;
   if (j < o.y0 || j >= o.y1) {
     long long vs;
-    const S *p = ovl_halo_src<NV, N>(a, W, o, X, j, vs);
+    const S *p = ovl_halo_src<NV, N, TY>(a, o, X, j, vs);
 #pragma unroll
     for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * vs);
   } else if (o.flags & kPercell) {
-    lring_issue_cells<A, V, NV, D>(a, W, X, o, rg, slot, j);
+    lring_issue_cells<A, V, NV, D, TY>(a, W, X, o, rg, slot, j);
   } else {
-    const S *p = o.op + (long long)(j - o.y0) * o.ors;
+    int ors;
+    long long ovs;
+    if constexpr (N < 4) {
+      ors = o.ors;
+      ovs = o.ovs;
+    } else {
+      ors = (o.flags & kOwnStrip) ? N : (o.flags & kOwnDir) ? 0 : (int)a.pitch;
+      ovs = (o.flags & kOwnStrip) ? (long long)TY * N : (o.flags & kOwnDir) ? (long long)N : a.plane;
+    }
+    const S *p = o.op + (long long)(j - o.y0) * ors;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * o.ovs);
+    for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * ovs);
   }
   cp_async_commit();
 }
@@ -991,7 +1034,7 @@ static __device__ __forceinline__ void lring_read(const LaneRing<typename Ops<A>
 // lane has issued rows up to r + D - 2 and waits until at most D - 2 copy
 // groups are pending, i.e. row r has landed.  A slot is refilled only after
 // the row read from it has been consumed by the flux computation.
-template <class Sys, class A, int V, int D, bool FIN, bool INPL = false, class G>
+template <class Sys, class A, int V, int D, bool FIN, bool INPL = false, int TYC = 0, class G>
 static __device__ __forceinline__ void march_async(const G &a, const SysParams<A> &P,
                                                    const typename Ops<A>::S *src,
                                                    typename Ops<A>::S *dst,
@@ -1005,7 +1048,7 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
   S *dst_lane = dst + X;
   const int nrows = y1 - y0 + 2;
   auto issue = [&](int r, int j) {
-    if (INPL) lring_issue_inplace<A, V, NV, D>(a, src, X, *ovl, rg, r, j);
+    if constexpr (INPL) lring_issue_inplace<A, V, NV, D, TYC>(a, src, X, *ovl, rg, r, j);
     else lring_issue<A, V, NV, D>(a, src, X, xin, rg, r, j);
   };
   // prologue: rows 0 .. D-2 in flight (empty groups past the end keep the count)
@@ -1048,7 +1091,7 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       read(r, RA.W);
-      advance_row<Sys, A, V, false, FIN, INPL>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad, xin, ovl);
+      advance_row<Sys, A, V, false, FIN, INPL, TYC>(a, P, dst_lane, X, j, writer, lx, ly, RB, RA, Fs, lam_loc, bad, xin, ovl);
       if (r + D - 1 < nrows) issue(r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
@@ -1058,7 +1101,7 @@ static __device__ __forceinline__ void march_async(const G &a, const SysParams<A
       const int r = j - y0 + 2;
       cp_async_wait<D - 2>();
       read(r, RB.W);
-      advance_row<Sys, A, V, false, FIN, INPL>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad, xin, ovl);
+      advance_row<Sys, A, V, false, FIN, INPL, TYC>(a, P, dst_lane, X, j, writer, lx, ly, RA, RB, Fs, lam_loc, bad, xin, ovl);
       if (r + D - 1 < nrows) issue(r + D - 1, y0 - 1 + r + D - 1);
       else cp_async_commit();
     }
@@ -1140,20 +1183,11 @@ fv_step_kernel(const StepArgs<typename Ops<A>::S> a) {
       const bool xin = __all_sync(0xffffffffu, X >= 0 && X + N <= a.nx);
       if constexpr (INPL && D < 0) {
         Ovl<S> o;
-        o.rd = a.ovl[n & 1];
-        o.wr = a.ovl[(n + 1) & 1];
-        o.sx = sx_;
-        o.cy = cy;
-        o.nstrips = a.nstrips;
-        o.nchunks = a.nchunks;
-        o.X0 = sx_ * (30 * N);
+        o.task = task;
         o.y0 = y0;
         o.y1 = y1;
-        o.ty = TY;
-        o.ts = a.ovl_task;
-        o.dstrip = a.ovl_bc;
-        ovl_lane_setup<NV, N>(a, src, o, X, lane);
-        march_async<Sys, A, V, DA, FIN, true>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad, &o);
+        ovl_lane_setup<NV, N, TY>(a, src, o, X, lane, sx_, cy, n);
+        march_async<Sys, A, V, DA, FIN, true, TY>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad, &o);
       } else {
         if (D > 0 && xin) march_tma<Sys, A, V, DT, FIN>(a, P, src, dst, rg, X, y0, y1, writer, lx, ly, lam_loc, bad);
         else if (D < 0) march_async<Sys, A, V, DA, FIN>(a, P, src, dst, lrg, X, xin, y0, y1, writer, lx, ly, lam_loc, bad);

@@ -58,6 +58,36 @@ def test_inplace_equals_two_buffers_bitwise(precision, bc, shape):
     assert t1 == t0
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("bc", ["mixed", "dirichlet", "transmissive"])
+def test_every_inplace_candidate_equals_two_buffers(precision, bc):
+    """Every compiled in-place candidate (cells per lane, rows per task,
+    blocks per SM, ring depth) gives the two-buffer mode's bits."""
+    f = fv()
+    prim, d = wl.random_smooth_euler(193, seed=11, ny=141)
+    d = dict(d, **BCS[bc])
+    W0, t0, _ = run(d, prim, 17, precision, False)
+    names = []
+    k = 0
+    while True:
+        try:
+            s = f.Solver(d, precision, tune=2 + k)
+        except f.FvError:
+            break
+        with s:
+            try:
+                s.set_inplace(True)
+            except f.FvError:
+                break
+            s.set_state(prim, primitive=True)
+            s.run(17)
+            names.append(s.kernel_info()[1])
+            assert np.array_equal(s.state(), W0), names[-1]
+            assert s.time() == t0
+        k += 1
+    assert len(names) >= 2 and all("inplace" in n for n in names)
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_inplace_advection_equals_two_buffers(precision):
     prim, d = wl.advection_bump(128)
