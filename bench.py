@@ -271,6 +271,15 @@ def oracle_sample(d, prim, steps, what):
             "status": int(r.status), "sample": f"{what}: {steps} FP64 steps of {d['nx']}x{d['ny']}, {el:.2f} s"}
 
 
+def job_config(desc, ncell, nsteps_job, ws):
+    """The workload both arms report (the kernel that ran is a key of its own)."""
+    f32_bytes = 4 * 4 * ncell  # one FP32 Euler state buffer
+    l2 = (f"inputs larger than L2 (state buffers {f32_bytes / 2**30:.3g} GiB f32 / {2 * f32_bytes / 2**30:.3g} GiB f64)"
+          if f32_bytes > 129e6 else "state within L2 (a small workload: no flush between steps)")
+    return {"workload": desc, "cells": ncell, "time_steps_per_bench_step": nsteps_job, "l2": l2,
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -302,7 +311,7 @@ def run_reference(args):
             "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "sample_steps_per_bench_step": per},
+            "config": job_config(desc, ncell, nsteps_job, ws),
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.max_threads(), "cpu": cpu_model(),
                              "kind": "oracle",
                              "sample": f"{per} FV steps of the full {d['nx']}x{d['ny']} grid per bench step"},
@@ -684,10 +693,8 @@ def main():
            "value": value32, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": desc, "cells": ncell, "time_steps_per_bench_step": nsteps_job,
-                      "kernel": kinfo32, "kernel_choice": choices.get("f32"),
-                      "l2": "inputs larger than L2 (state buffers 1 GiB f32 / 2 GiB f64)",
-                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "config": job_config(desc, ncell, nsteps_job, ws),
+           "kernel": kinfo32, "kernel_choice": choices.get("f32"),
            "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm, "unit": "GB/s",
                         "frac": achieved32 / hbm, "frac_nominal": achieved32 / NOMINAL_HBM_GBS,
                         "traffic": (None if measured_traffic_per_cell(kinfo32) is None
