@@ -512,6 +512,40 @@ template <class A, int V, int NV> struct RowState {
   A dX[V][NV];
 };
 
+// The y-faces between rows j (cur) and j+1 (nxt), evaluated once, and the
+// updated values of row j: Fs holds the south faces of row j on entry and
+// those of row j+1 on return.  FP64 Euler and spray on square cells take
+// fv_update_sq (lx == ly: every kernel computes lx and ly the same way, so
+// every kernel takes the same form on the same grid); the scalar advection
+// kernels, bound by latency rather than by the FP64 pipe, keep the general
+// form.
+template <class Sys, class A, int V>
+static __device__ __forceinline__ void faces_update_row(const RowState<A, V, Sys::NV> &cur,
+                                                        const RowState<A, V, Sys::NV> &nxt, A (&Fs)[V][Sys::NV],
+                                                        A lx, A ly, A (&Wn)[V][Sys::NV]) {
+  using O = Ops<A>;
+  auto run = [&](auto sq) {
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+      const A sg = O::max(cur.sy[c], nxt.sy[c]);
+#pragma unroll
+      for (int v = 0; v < Sys::NU; ++v) {
+        const A Fn = lf_face2(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], sg);
+        const A dY = O::sub(Fn, Fs[c][v]);
+        if constexpr (decltype(sq)::value) Wn[c][v] = fv_update_sq(cur.W[c][v], cur.dX[c][v], dY, lx);
+        else Wn[c][v] = fv_update(cur.W[c][v], cur.dX[c][v], dY, lx, ly);
+        Fs[c][v] = Fn;
+      }
+    }
+  };
+  if constexpr (std::is_same<A, double>::value && Sys::NV > 1) {
+    if (lx == ly) run(std::true_type{});
+    else run(std::false_type{});
+  } else {
+    run(std::false_type{});
+  }
+}
+
 // Compute part of one row of the march (rows j and j+1 in registers): x-work
 // of row j+1, the y-face between rows j and j+1 evaluated once, update and
 // store of row j (by the writer lanes), and the new state's wave speed.
@@ -528,16 +562,7 @@ static __device__ __forceinline__ void advance_row(const G &a, const SysParams<A
   using O = Ops<A>;
   row_x<Sys, V>(P, nxt.W, nxt.Fy, nxt.sy, nxt.dX);
   A Wn[V][NV];
-#pragma unroll
-  for (int c = 0; c < V; ++c) {
-    const A sg = O::max(cur.sy[c], nxt.sy[c]);
-#pragma unroll
-    for (int v = 0; v < Sys::NU; ++v) {
-      const A Fn = lf_face2(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], sg);
-      Wn[c][v] = fv_update(cur.W[c][v], cur.dX[c][v], O::sub(Fn, Fs[c][v]), lx, ly);
-      Fs[c][v] = Fn;
-    }
-  }
+  faces_update_row<Sys, A, V>(cur, nxt, Fs, lx, ly, Wn);
   // carried planes (primitives of the new state) follow from the updated ones
   if constexpr (Sys::NU != Sys::NV) {
 #pragma unroll

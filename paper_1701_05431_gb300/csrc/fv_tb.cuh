@@ -185,16 +185,8 @@ static __device__ __forceinline__ void tb_level_row(const SysParams<A> &P, RowSt
                                                     A (&Wn)[V][Sys::NV]) {
   using O = Ops<A>;
   row_x<Sys, V>(P, nxt.W, nxt.Fy, nxt.sy, nxt.dX);
-#pragma unroll
-  for (int c = 0; c < V; ++c) {
-    const A sg = O::max(cur.sy[c], nxt.sy[c]);
-#pragma unroll
-    for (int v = 0; v < Sys::NV; ++v) {
-      const A Fn = lf_face2(cur.W[c][v], cur.Fy[c][v], nxt.W[c][v], nxt.Fy[c][v], sg);
-      Wn[c][v] = fv_update(cur.W[c][v], cur.dX[c][v], O::sub(Fn, Fs[c][v]), lx, ly);
-      Fs[c][v] = Fn;
-    }
-  }
+  static_assert(Sys::NU == Sys::NV, "two-step passes carry no planes");
+  faces_update_row<Sys, A, V>(cur, nxt, Fs, lx, ly, Wn);
 }
 
 // A level-1 row as the state stores it: rounded to the storage type, as a
