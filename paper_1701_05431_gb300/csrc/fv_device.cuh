@@ -299,9 +299,11 @@ struct Euler {
     R inv = O::rcp(W[0]);
     u = O::mul(W[1], inv);
     v = O::mul(W[2], inv);
-    // kinetic energy: a plain sum of two rounded products keeps x <-> y symmetry
-    R ke = O::mul(O::splat(0.5), O::add(O::mul(W[1], u), O::mul(W[2], v)));
-    p = O::mul(P.p1, O::sub(W[3], ke));
+    // twice the kinetic energy: a plain sum of two rounded products keeps
+    // x <-> y symmetry; p = (gamma - 1) rho E - ((gamma - 1)/2) (that sum),
+    // the second product fused
+    const R s = O::add(O::mul(W[1], u), O::mul(W[2], v));
+    p = O::fma(O::neg(O::mul(O::splat(0.5), P.p1)), s, O::mul(P.p1, W[3]));
     c = O::sqrt(O::mul(O::mul(P.p0, p), inv));
   }
   template <class R>
