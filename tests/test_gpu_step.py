@@ -221,10 +221,19 @@ def test_constant_state_bitwise(precision, bc):
     assert np.array_equal(out, W0)
 
 
+def rows_per_task(info: str) -> int:
+    """Rows per warp task of a kernel description: the balanced count when
+    the host reports one (", N-row tasks"), else the candidate's TY."""
+    import re
+    m = re.search(r", (\d+)-row tasks", info)
+    return int(m.group(1)) if m else int(re.search(r" ty(\d+)", info).group(1))
+
+
 def test_default_kernel_fills_the_gpu_on_small_grids():
     """Without tuning, a large grid gets the first candidate; a grid whose
-    warp tasks cannot fill the GPU with it gets a candidate with shorter
-    tasks."""
+    warp tasks cannot fill the GPU with it gets shorter tasks: another
+    candidate, its rows per task balanced over the GPU where the host does
+    that."""
     f = fv()
     for precision in ("f32", "f64", "bf16"):
         first = f.kernel_candidates("euler", precision)[0]
@@ -234,8 +243,9 @@ def test_default_kernel_fills_the_gpu_on_small_grids():
             # FP64 kernels may report rows per task balanced over the GPU
             assert s.kernel_info()[1].split(",")[0] == first
         with f.Solver(small, precision) as s:
-            got = s.kernel_info()[1].split(",")[0]
-        assert got != first and "ty16" in got, (precision, got)
+            info = s.kernel_info()[1]
+        got = info.split(",")[0]
+        assert got != first and rows_per_task(info) < rows_per_task(first), (precision, info)
 
 
 def test_periodic_conservation_fp64_and_fp32_drift():
