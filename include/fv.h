@@ -163,8 +163,10 @@ fv_status fv_get_state(fv_ctx *ctx, void *dst, int dst_is_device, int dst_dtype)
  * as it was and the steps from there run one at a time.  fv_run uses passes
  * when t_end <= 0 and at least two steps remain.  steps_per_pass = 1 turns
  * it off.  With tune >= 2 the (tune - 2)-th two-step kernel candidate is
- * used (FV_ERR_INVALID_ARG past the last one), else the first that fills
- * the GPU.  Errors: FV_ERR_INVALID_ARG when a condition above fails. */
+ * used (FV_ERR_INVALID_ARG past the last one); otherwise the recorded
+ * kernel table's two-step entry for the grid (tune = 0), else the first
+ * candidate that fills the GPU.  Errors: FV_ERR_INVALID_ARG when a condition
+ * above fails. */
 fv_status fv_set_time_blocking(fv_ctx *ctx, int steps_per_pass);
 
 /* In-place mode (on != 0; advection and Euler, every precision): the
@@ -178,8 +180,10 @@ fv_status fv_set_time_blocking(fv_ctx *ctx, int steps_per_pass);
  * allocates again (off) the second state buffer and keeps the current state,
  * time and step.  Autotuning (tune = 1) is not done in place; with
  * tune >= 2 the (tune - 2)-th in-place kernel candidate is used
- * (FV_ERR_INVALID_ARG past the last one), else the first that fills the GPU.
- * Errors: FV_ERR_INVALID_ARG (spray system), FV_ERR_OOM, FV_ERR_CUDA. */
+ * (FV_ERR_INVALID_ARG past the last one); otherwise the recorded kernel
+ * table's in-place entry for the grid (tune = 0), else the first candidate
+ * that fills the GPU.  Errors: FV_ERR_INVALID_ARG (spray system),
+ * FV_ERR_OOM, FV_ERR_CUDA. */
 fv_status fv_set_inplace(fv_ctx *ctx, int on);
 
 /* Asynchronous snapshot of the current state W^n, the counterpart of the
