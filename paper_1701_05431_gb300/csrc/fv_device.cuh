@@ -306,12 +306,12 @@ struct Euler {
     p = O::fma(O::neg(O::mul(O::splat(0.5), P.p1)), s, O::mul(P.p1, W[3]));
     c = O::sqrt(O::mul(O::mul(P.p0, p), inv));
   }
+  // The fluxes and speeds of a cell from its primitives q = (u, v, p, c).
   template <class R>
-  static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
-                                                R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {
+  static __device__ __forceinline__ void fluxes_from(const R (&W)[NV], const R (&q)[4], R (&Fx)[NV], R &sx,
+                                                     R (&Fy)[NV], R &sy) {
     using O = Ops<R>;
-    R u, v, p, c;
-    prims(W, P, u, v, p, c);
+    const R u = q[0], v = q[1], p = q[2], c = q[3];
     R Ep = O::add(W[3], p);
     Fx[0] = W[1];
     Fx[1] = O::fma(W[1], u, p);
@@ -324,14 +324,30 @@ struct Euler {
     sx = O::add(O::abs(u), c);
     sy = O::add(O::abs(v), c);
   }
+  // The wave speed and admissibility of a cell from its primitives.
+  template <class R>
+  static __device__ __forceinline__ R lambda_from(const R (&W)[NV], const R (&q)[4], unsigned &bad) {
+    using O = Ops<R>;
+    R l = O::add(O::max(O::abs(q[0]), O::abs(q[1])), q[3]);
+    bad = O::not_pos(W[0]) | O::not_pos(q[2]) | O::not_fin(l);
+    return l;
+  }
+  template <class R>
+  static __device__ __forceinline__ void prims4(const R (&W)[NV], const SysParams<R> &P, R (&q)[4]) {
+    prims(W, P, q[0], q[1], q[2], q[3]);
+  }
+  template <class R>
+  static __device__ __forceinline__ void fluxes(const R (&W)[NV], const SysParams<R> &P,
+                                                R (&Fx)[NV], R &sx, R (&Fy)[NV], R &sy) {
+    R q[4];
+    prims4(W, P, q);
+    fluxes_from(W, q, Fx, sx, Fy, sy);
+  }
   template <class R>
   static __device__ __forceinline__ R lambda(const R (&W)[NV], const SysParams<R> &P, unsigned &bad) {
-    using O = Ops<R>;
-    R u, v, p, c;
-    prims(W, P, u, v, p, c);
-    R l = O::add(O::max(O::abs(u), O::abs(v)), c);
-    bad = O::not_pos(W[0]) | O::not_pos(p) | O::not_fin(l);
-    return l;
+    R q[4];
+    prims4(W, P, q);
+    return lambda_from(W, q, bad);
   }
 };
 

@@ -253,14 +253,19 @@ static __device__ __forceinline__ void load_row(const G &a,
 // the west-face flux of each cell (the first cell's west neighbour is the
 // previous lane's last cell), the east face from the next lane, and
 // dX = F~_{i+1/2} - F~_{i-1/2}.  Also returns the y-fluxes and y-speeds.
-template <class Sys, int V, class A>
+// USEQ: the cells' primitives are given in Q (Euler), not recovered here.
+template <class Sys, int V, bool USEQ = false, class A>
 static __device__ __forceinline__ void row_x(const SysParams<A> &P, const A (&W)[V][Sys::NV],
-                                             A (&Fy)[V][Sys::NV], A (&sy)[V], A (&dX)[V][Sys::NV]) {
+                                             A (&Fy)[V][Sys::NV], A (&sy)[V], A (&dX)[V][Sys::NV],
+                                             const A (*Q)[4] = nullptr) {
   constexpr int NV = Sys::NV;
   using O = Ops<A>;
   A Fx[V][NV], sx[V];
 #pragma unroll
-  for (int c = 0; c < V; ++c) Sys::fluxes(W[c], P, Fx[c], sx[c], Fy[c], sy[c]);
+  for (int c = 0; c < V; ++c) {
+    if constexpr (USEQ) Sys::fluxes_from(W[c], Q[c], Fx[c], sx[c], Fy[c], sy[c]);
+    else Sys::fluxes(W[c], P, Fx[c], sx[c], Fy[c], sy[c]);
+  }
   A Fw[V][NV];
 #pragma unroll
   for (int c = 0; c < V; ++c) {

@@ -179,12 +179,11 @@ static __device__ __forceinline__ void tb_fix_cols(const G &a, A (&W)[V][NV], in
 // One row of one level: x-work of `nxt`, the y-face between `cur` and `nxt`,
 // and the updated values of `cur`'s row for every lane (the arithmetic of
 // advance_row, without the store).
-template <class Sys, class A, int V>
+template <class Sys, class A, int V, bool USEQ = false>
 static __device__ __forceinline__ void tb_level_row(const SysParams<A> &P, RowState<A, V, Sys::NV> &cur,
                                                     RowState<A, V, Sys::NV> &nxt, A (&Fs)[V][Sys::NV], A lx, A ly,
-                                                    A (&Wn)[V][Sys::NV]) {
-  using O = Ops<A>;
-  row_x<Sys, V>(P, nxt.W, nxt.Fy, nxt.sy, nxt.dX);
+                                                    A (&Wn)[V][Sys::NV], const A (*Q)[4] = nullptr) {
+  row_x<Sys, V, USEQ>(P, nxt.W, nxt.Fy, nxt.sy, nxt.dX, Q);
   static_assert(Sys::NU == Sys::NV, "two-step passes carry no planes");
   faces_update_row<Sys, A, V>(cur, nxt, Fs, lx, ly, Wn);
 }
@@ -227,6 +226,34 @@ static __device__ __forceinline__ void tb_lambda(const SysParams<A> &P, const A 
   }
 }
 
+// The same from the cells' primitives Q (Euler): the bits of tb_lambda.
+template <class Sys, class A, int V>
+static __device__ __forceinline__ void tb_lambda_q(const A (&Wn)[V][Sys::NV], const A (&Q)[V][4], int X, int nx,
+                                                   bool writer, typename Ops<A>::P &lam, unsigned &bad) {
+  using O = Ops<A>;
+  if (!writer) return;
+#pragma unroll
+  for (int c = 0; c < V; ++c) {
+    const unsigned valid = X + c < nx ? 1u : 0u;
+    unsigned b;
+    const A l = Sys::lambda_from(Wn[c], Q[c], b);
+    lam = fmax(lam, O::hmax(l, valid));
+    bad |= b & valid;
+  }
+}
+
+// Level 1's rows feed level 2 as they are produced: with FP32 or FP64
+// storage (no rounding between the levels) the primitives of a level-1 row
+// serve both its wave-speed check and level 2's fluxes of that row, one
+// recovery instead of two.  The ghost columns and rows are set first, so
+// the primitives are those of the row level 2 reads; the check only looks at
+// cells inside the grid, which the ghosts leave alone.
+template <class Sys, class A>
+struct TbReuse {
+  static constexpr bool value = std::is_same<Sys, Euler>::value &&
+                                (std::is_same<A, float>::value || std::is_same<A, double>::value);
+};
+
 template <class Sys, class A, int V, class G>
 static __device__ __forceinline__ void tb_store(const G &a, const A (&Wn)[V][Sys::NV], typename Ops<A>::S *dst_lane,
                                                 int X, int j, bool writer) {
@@ -260,6 +287,7 @@ static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &
                                                 typename Ops<A>::P &lam2, unsigned &bad2) {
   using S = typename Ops<A>::S;
   constexpr int NV = Sys::NV;
+  constexpr bool REUSE = TbReuse<Sys, A>::value;
   using O = Ops<A>;
   S *dst_lane = dst + X;
   // ghost rows of W^{n+1} below row 0 and above row ny - 1 on non-periodic
@@ -344,7 +372,9 @@ static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &
     if (k > y1) break;
     fetch(k - y0 + 3, R1a.W);
     tb_level_row<Sys, A, V>(P, R1b, R1a, Fs1, lx, ly, Wn);
-    if (k < y1) tb_lambda<Sys, A, V>(P, Wn, X, a.nx, writer, lam1, bad1);
+    if constexpr (!REUSE) {
+      if (k < y1) tb_lambda<Sys, A, V>(P, Wn, X, a.nx, writer, lam1, bad1);
+    }
     tb_round_to_storage<A, V, NV>(Wn);
     if constexpr (NP) tb_fix_cols<A, V, NV>(a, Wn, X, X0, lane);
 #pragma unroll
@@ -362,14 +392,24 @@ static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &
           for (int v = 0; v < NV; ++v) R2a.W[c][v] = R2b.W[c][v];
       }
     }
-    tb_level_row<Sys, A, V>(P, R2b, R2a, Fs2, lx, ly, Wm);
+    if constexpr (REUSE) {
+      A Q[V][4];
+#pragma unroll
+      for (int c = 0; c < V; ++c) Sys::prims4(R2a.W[c], P, Q[c]);
+      if (k < y1) tb_lambda_q<Sys, A, V>(R2a.W, Q, X, a.nx, writer, lam1, bad1);
+      tb_level_row<Sys, A, V, true>(P, R2b, R2a, Fs2, lx, ly, Wm, Q);
+    } else {
+      tb_level_row<Sys, A, V>(P, R2b, R2a, Fs2, lx, ly, Wm);
+    }
     tb_store<Sys, A, V>(a, Wm, dst_lane, X, k - 1, writer);
     tb_lambda<Sys, A, V>(P, Wm, X, a.nx, writer, lam2, bad2);
     ++k;
     if (k > y1) break;
     fetch(k - y0 + 3, R1b.W);
     tb_level_row<Sys, A, V>(P, R1a, R1b, Fs1, lx, ly, Wn);
-    if (k < y1) tb_lambda<Sys, A, V>(P, Wn, X, a.nx, writer, lam1, bad1);
+    if constexpr (!REUSE) {
+      if (k < y1) tb_lambda<Sys, A, V>(P, Wn, X, a.nx, writer, lam1, bad1);
+    }
     tb_round_to_storage<A, V, NV>(Wn);
     if constexpr (NP) tb_fix_cols<A, V, NV>(a, Wn, X, X0, lane);
 #pragma unroll
@@ -386,7 +426,15 @@ static __device__ __forceinline__ void march_tb(const G &a, const SysParams<A> &
           for (int v = 0; v < NV; ++v) R2b.W[c][v] = R2a.W[c][v];
       }
     }
-    tb_level_row<Sys, A, V>(P, R2a, R2b, Fs2, lx, ly, Wm);
+    if constexpr (REUSE) {
+      A Q[V][4];
+#pragma unroll
+      for (int c = 0; c < V; ++c) Sys::prims4(R2b.W[c], P, Q[c]);
+      if (k < y1) tb_lambda_q<Sys, A, V>(R2b.W, Q, X, a.nx, writer, lam1, bad1);
+      tb_level_row<Sys, A, V, true>(P, R2a, R2b, Fs2, lx, ly, Wm, Q);
+    } else {
+      tb_level_row<Sys, A, V>(P, R2a, R2b, Fs2, lx, ly, Wm);
+    }
     tb_store<Sys, A, V>(a, Wm, dst_lane, X, k - 1, writer);
     tb_lambda<Sys, A, V>(P, Wm, X, a.nx, writer, lam2, bad2);
     ++k;
