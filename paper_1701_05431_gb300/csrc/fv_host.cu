@@ -189,14 +189,6 @@ static fv_status validate(const fv_config *c) {
   return FV_OK;
 }
 
-// Default kernel per (system, precision): the first registered candidate.
-static int default_variant(int system, int prec) {
-  const auto &vs = all_variants();
-  for (size_t k = 0; k < vs.size(); ++k)
-    if (vs[k].system == system && vs[k].precision == prec && !vs[k].inplace && !vs[k].tb) return (int)k;
-  return -1;
-}
-
 // Blocks of a kernel candidate resident per SM (its register target MINB if
 // the occupancy query fails).
 static int resident_blocks(const Variant &V) {
