@@ -451,18 +451,15 @@ template <class A, int V, int NV, class G, class S>
 static __device__ __forceinline__ void ovl_fix_cols(const G &a, const Ovl<S> &o, A (&W)[V][NV], int lane) {
   using O = Ops<A>;
   static_assert(O::K == 1, "in-place kernels hold one cell per value");
-  if (o.flags & (3u << kFixWShift)) {
+  if (o.flags & ((3u << kFixWShift) | (3u << kFixEShift))) {
+    const bool fw = lane == 0 && (o.flags & (3u << kFixWShift));
+    const bool fe = lane == 31 && (o.flags & (3u << kFixEShift));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const A w0 = O::shfl_down(W[0][v], 1);
-      if (lane == 0) W[V - 1][v] = w0;
-    }
-  }
-  if (o.flags & (3u << kFixEShift)) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
       const A wl = O::shfl_up(W[V - 1][v], 1);
-      if (lane == 31) W[0][v] = wl;
+      if (fw) W[V - 1][v] = w0;
+      if (fe) W[0][v] = wl;
     }
   }
 }
@@ -1002,12 +999,13 @@ static __device__ __forceinline__ void lring_issue_inplace(const G &a, const typ
   using S = typename Ops<A>::S;
   constexpr int N = V * Ops<A>::K;
   const int slot = r % D;
-  if (j < o.y0 || j >= o.y1) {
+  const bool own = j >= o.y0 && j < o.y1;
+  if (!own) {
     long long vs;
     const S *p = ovl_halo_src<NV, N, TY>(a, o, X, j, vs);
 #pragma unroll
     for (int v = 0; v < NV; ++v) cp_async_cells<S, N>(rg.slot(slot, v), p + v * vs);
-  } else if (o.flags & kPercell) {
+  } else if (__builtin_expect((o.flags & kPercell) != 0u, 0)) {
     lring_issue_cells<A, V, NV, D, TY>(a, W, X, o, rg, slot, j);
   } else {
     int ors;
